@@ -1,0 +1,361 @@
+"""Benchmark: exhaustive Goldbach verification of [4, 10^10] on the GPU.
+
+One step = one gb_verify_range call over every even n of the workload:
+segment sieve of the q window, the loop-inverted cover with P1 = 2^15, the GPU
+retry pass to P2 = 2^20, per-segment reductions (GoldbachGPU, arXiv
+2603.02621, Sec. 2.3; Table 4 reports the same workload's exhaustive run).
+
+Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): rank r verifies its own
+range [4 + r*10^10, 4 + (r+1)*10^10 - 2) -- independent work, no collective on
+the data path (weak scaling); the timing is the max over ranks.
+
+--impl reference times the CPU oracle (oracle/) on a bounded sample of the
+same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "even integers verified/sec"
+UNIT = "even n/s"
+SEG = 1 << 24
+P1, P2 = 1 << 15, 1 << 20
+SPAN = 10**10                       # even n per rank: SPAN/2 - 1
+PAPER_NPS = 4999999999 / 23.547     # Table 4: [4, 1e10] in 23,547 ms on an RTX 3070
+
+
+def rank_range(rank: int):
+    lo = 4 + rank * SPAN
+    return lo, lo + SPAN - 2        # [4, 1e10 + 2) for rank 0: 4,999,999,999 even n
+
+
+def workload_desc(world: int):
+    return {"workload": "exhaustive Goldbach verification of every even n in [4, 1e10] per GPU",
+            "ranges": [list(rank_range(r)) for r in range(world)],
+            "seg_len": SEG, "base_primes_to": "isqrt(hi)+ (>= 1e5)", "p1": P1, "p2": P2,
+            "outputs": "per-segment p_min histogram (3512 entries), max p_min with n, unresolved",
+            "l2": "q window 625 MB per GPU > 126 MB L2; no flush needed"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(x: float, world: int, backend_ready: bool):
+    if world == 1 or not backend_ready:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, backend_ready: bool):
+    if world > 1 and backend_ready:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- cpu baseline
+def cpu_baseline(min_seconds: float = 12.0, seed: int = 11):
+    """The oracle, as it stands, on a bounded sample of the workload's segments."""
+    from oracle import oracle
+    from paper_2603_02621_gb300 import workloads
+    lo, hi = rank_range(0)
+    nseg = ((hi - lo) // 2 + SEG - 1) // SEG
+    threads = oracle.default_threads()
+    order = workloads.sample_indices(nseg, nseg, seed=seed)
+    rng = workloads.SplitMix64(seed)
+    for i in range(len(order) - 1, 0, -1):          # seeded shuffle of the segment order
+        j = rng.below(i + 1)
+        order[i], order[j] = order[j], order[i]
+    hl = 3512
+    import concurrent.futures as cf
+
+    def one(k):
+        # one sampled segment, verified by the oracle in one thread
+        a = lo + 2 * k * SEG
+        b = min(a + 2 * SEG, hi)
+        s, _ = oracle.verify_segments(a, b, SEG, P2, hl, threads=1)
+        return int(s[:, 0].sum())
+
+    done_n, t0, used = 0, time.perf_counter(), []
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        while time.perf_counter() - t0 < min_seconds and len(used) < nseg:
+            batch = order[len(used):len(used) + threads]
+            done_n += sum(ex.map(one, batch))
+            used += batch
+    dt = time.perf_counter() - t0
+    return {"value": done_n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(used)} seeded segments of 2^24 even n from [4, 1e10] "
+                      f"({done_n} n, {dt:.1f} s wall, P = 2^20)",
+            "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    per_step = max(4.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(min_seconds=1.0)
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(min_seconds=per_step)
+        vals.append(last["value"])
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * (SPAN // 2 - 1) / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_NPS,
+            "dtype": "u64", "data": "synthetic", "config": workload_desc(1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    from paper_2603_02621_gb300 import gb
+
+    torch.cuda.set_device(local)
+    backend_ready = False
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        backend_ready = True
+    stream = torch.cuda.current_stream()
+    lo, hi = rank_range(rank)
+    base = max(10**5, math.isqrt(hi + 4096) + 1)
+    ctx = gb.Context(device=local, base_limit=base, seg_len=SEG, p1=P1, p2=P2,
+                     stream=stream.cuda_stream)
+    nseg = ((hi - lo) // 2 + SEG - 1) // SEG
+    HL = 3512                                       # pi(2^15): per-segment row length
+    n_per_step = (hi - lo) // 2
+
+    # device-resident outputs for the device-timed value
+    d_rows = torch.zeros((nseg, HL), dtype=torch.int64, device="cuda")
+    d_segs = torch.zeros((nseg, 6), dtype=torch.int64, device="cuda")      # 48-byte records
+
+    def step_device():
+        r = gb.gb_range_result()
+        r.seg_hist = ctypes_ptr(d_rows)
+        r.seg_hist_stride = HL
+        r.seg_cap = nseg
+        r.segs = ctypes_segs(d_segs)
+        rc = gb.load().gb_verify_range(ctx.handle, lo, hi, 0, gb.ctypes.byref(r))
+        if rc:
+            raise gb.GbError(rc, "gb_verify_range", gb.gb_last_error())
+        return r
+
+    # pinned host outputs for the end-to-end number
+    h_rows = torch.zeros((nseg, HL), dtype=torch.int64).pin_memory()
+    h_segs = torch.zeros((nseg, 6), dtype=torch.int64).pin_memory()
+    h_hist = torch.zeros(HL, dtype=torch.int64).pin_memory()
+
+    def step_host():
+        r = gb.gb_range_result()
+        r.seg_hist = ctypes_ptr(h_rows)
+        r.seg_hist_stride = HL
+        r.seg_cap = nseg
+        r.segs = ctypes_segs(h_segs)
+        r.hist = ctypes_ptr(h_hist)
+        r.hist_cap = HL
+        rc = gb.load().gb_verify_range(ctx.handle, lo, hi, 0, gb.ctypes.byref(r))
+        if rc:
+            raise gb.GbError(rc, "gb_verify_range", gb.gb_last_error())
+        return r
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region (value), per-kernel events, clocks
+    clocks = ClockSampler(local)
+    gb.gb_profile_enable(ctx.handle, True)
+    barrier(world, backend_ready)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        last = step_device()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world, backend_ready)
+    dev_ms = ev0.elapsed_time(ev1)
+    prof = gb.gb_profile_read(ctx.handle)
+    work = gb.gb_profile_work(ctx.handle)
+    gb.gb_profile_enable(ctx.handle, False)
+    max_ms = reduce_max(dev_ms, world, backend_ready)
+
+    # ---- end-to-end region through the public call with pinned host buffers
+    barrier(world, backend_ready)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_ms = 1000.0 * (time.perf_counter() - t0)
+    e2e_ms = reduce_max(e2e_ms, world, backend_ready)
+
+    total_n = n_per_step * args.steps * world
+    value = total_n / (max_ms / 1000.0)
+    e2e_value = total_n / (e2e_ms / 1000.0)
+    d2h = 32 + nseg * 48 + nseg * HL * 8 + HL * 8
+
+    # ---- roofline of the dominant kernel (per-launch averages over the timed region)
+    peaks, peak_src = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    kern = max(("sieve", "cover"), key=lambda k: prof[k]["ms"])
+    kp = prof[kern]
+    launches = max(1, kp["launches"])
+    per_launch_ms = kp["ms"] / launches
+    # integer issue peak: 152 SMs x 4 schedulers x 32 lanes x f_max
+    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12            # T lane-ops/s
+    if kern == "cover":
+        ops_per_unit, units = 8.0, work["cover_iterations"]
+        unit_name = "cover word-iterations (8 lane-ops each)"
+    else:
+        ops_per_unit, units = 4.0, work["sieve_strikes"]
+        unit_name = "sieve strikes (4 lane-ops each)"
+    achieved = ops_per_unit * (units / launches) / (per_launch_ms / 1000.0) / 1e12
+    hbm_bytes = (kp["units"] / launches) / 8.0            # q bits written (sieve) or n read (cover) / 8
+    hbm_achieved = hbm_bytes / (per_launch_ms / 1000.0) / 1e9
+    roofline = {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+                "work": unit_name, "work_per_launch": units / launches,
+                "ms_per_launch": per_launch_ms,
+                "peak_source": "derived: 152 SMs x 128 lanes x %.0f MHz (%s max clock)" % (sm_max, peak_src),
+                "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+                        "frac": hbm_achieved / float(peaks.get("hbm_gbs", 6800.0)),
+                        "algorithmic_bytes_per_launch": hbm_bytes}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / (PAPER_NPS * world),
+            "dtype": "u64", "data": "synthetic", "mode": "plain",
+            "config": workload_desc(world),
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+            "clocks": clk,
+            "gpu_launches": int(sum(prof[k]["launches"] for k in prof)),
+            "kernel_ms": {k: prof[k]["ms"] for k in prof},
+            "result_check": {"unresolved": int(last.unresolved), "max_pmin": int(last.max_pmin),
+                             "max_pmin_n": int(last.max_pmin_n), "n_checked": int(last.n_checked)},
+            "paper_context": "RTX 3070, Table 4: [4, 1e10] in 23,547 ms = 2.12e8 n/s"}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline().items() if k != "seconds"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if backend_ready:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def ctypes_ptr(t):
+    from paper_2603_02621_gb300 import gb
+    return gb.ctypes.cast(gb.ctypes.c_void_p(t.data_ptr()), gb.POINTER(gb.c_uint64))
+
+
+def ctypes_segs(t):
+    from paper_2603_02621_gb300 import gb
+    return gb.ctypes.cast(gb.ctypes.c_void_p(t.data_ptr()), gb.POINTER(gb.gb_segment_result))
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * gb.h -- C ABI of libgb, a GB300 (sm_103a) implementation of the segmented
+ * double sieve and the loop-inverted Goldbach cover of GoldbachGPU
+ * (arXiv 2603.02621).
+ *
+ * The method (Sec. 2.3.1): instead of searching, for each even n, a prime p
+ * with n - p prime, iterate over the primes p and mark every even n whose
+ * partner q = n - p is prime.  The primality of every odd q in a window is
+ * held as an odd-only bitset (Sec. 2.2: one bit per odd number), produced
+ * here on the GPU by a segmented sieve of Eratosthenes (the GPU sieve that
+ * Sec. 4.5 names as future work).  The marking is the word-parallel form
+ * Sec. 4.3 names as future work: for p = 3, 5, 7, ... <= P in ascending order,
+ * a shifted copy of the q-bitset is OR-ed into a coverage bitset C over the
+ * even n, and the first p that sets an n's bit is that n's minimal Goldbach
+ * prime p_min(n) (Sec. 2.3.2).  n with no p <= P1 go to a second GPU pass up
+ * to P2 (replacing the CPU fallback of Sec. 2.3.3).
+ *
+ * Conventions (all entry points):
+ *   - return 0 (GB_OK) on success, a GB_E* code otherwise; gb_strerror()
+ *     names the code and gb_last_error() gives the last message of the
+ *     calling thread;
+ *   - ranges are half-open [lo, hi) over EVEN n; lo must be even and >= 4,
+ *     hi even and > lo.  "[4, N]" inclusive is [4, N + 2);
+ *   - prime index: the i-th prime with p_0 = 2, p_1 = 3, p_2 = 5, ...
+ *   - every buffer is owned by the caller; the library owns its device
+ *     arenas.  Pointers documented "host or device" are classified with
+ *     cudaPointerGetAttributes; host memory may be pageable or pinned;
+ *   - an n with no p <= the bound is DATA (counted as unresolved), not an
+ *     error;
+ *   - a context is bound to one device and one stream; calls on one
+ *     context must not overlap (not thread-safe per context).
+ */
+#ifndef GB_H
+#define GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GB_OK        0
+#define GB_EINVAL    1  /* bad argument: odd/short range, lo >= hi, hi beyond base_limit^2, P > p2, bad config */
+#define GB_ENOMEM    2  /* device or host allocation failed (or admission refused) */
+#define GB_ECUDA     3  /* a CUDA runtime call failed; gb_last_error() has the CUDA message */
+#define GB_ETIMEOUT  4  /* a bounded device wait gave up */
+#define GB_EBUSY     5  /* the context is in use */
+#define GB_ERANGE    6  /* an output buffer is too small; everything that fit was written */
+
+typedef struct gb_ctx gb_ctx;
+
+/* Context configuration.  Zero fields take the defaults given. */
+typedef struct gb_config {
+    int32_t  device;        /* CUDA device ordinal */
+    uint32_t seg_len;       /* S: even n per segment (equal to the odd q per
+                               segment).  Multiple of 2048; 0 = 2^24.  Segments
+                               are the unit of the per-segment outputs. */
+    uint64_t base_limit;    /* base primes are sieved to this bound at init;
+                               every range needs hi <= base_limit^2 (and
+                               base_limit >= the primes it needs, Sec. 2.3.1:
+                               a segmented sieve of [A, B] needs primes to
+                               sqrt(B)); 0 = 2^16; at most 2^32 */
+    uint32_t tile_bits;     /* segment-sieve tile (odd numbers per CTA tile),
+                               multiple of 8192, <= 2^20; 0 = 2^18 */
+    uint32_t cta_threads;   /* threads per sieve/cover CTA, multiple of 32,
+                               <= 1024; 0 = 256 */
+    uint32_t bucket_split;  /* sieving primes >= this go through per-tile hit
+                               lists; 0 = tile_bits */
+    uint32_t p1;            /* first-pass bound P1 (p <= P1); 0 = 2^15 */
+    uint32_t p2;            /* retry-pass bound P2; 0 or <= p1 = no retry pass;
+                               <= 2^24 */
+    uint64_t slab_bits;     /* most q-bits sieved and kept resident at once
+                               (a slab is a run of whole segments); 0 = 2^33 */
+    void*    stream;        /* cudaStream_t for all work; NULL = the legacy
+                               default stream */
+} gb_config;
+
+/* Per-segment output (Sec. 2.3.2): the segment holds the even n in [lo, hi). */
+typedef struct gb_segment_result {
+    uint64_t lo, hi;
+    uint64_t n_checked;     /* (hi - lo) / 2 */
+    uint64_t unresolved;    /* n with no prime p <= the final bound */
+    uint64_t max_pmin_n;    /* smallest n attaining max_pmin (0 if none) */
+    uint32_t max_pmin;      /* largest p_min found in the segment (0 if none) */
+    uint32_t hist_len;      /* 1 + prime index of max_pmin: entries of this
+                               segment's histogram row that can be nonzero */
+} gb_segment_result;
+
+/* Output of gb_verify_range: totals over the range plus optional detail. */
+typedef struct gb_range_result {
+    /* --- written by the library --- */
+    uint64_t n_checked;     /* (hi - lo) / 2 */
+    uint64_t unresolved;    /* n with no prime p <= the final bound */
+    uint64_t max_pmin_n;    /* smallest n attaining max_pmin (0 if none) */
+    uint32_t max_pmin;      /* largest p_min over the range (0 if none) */
+    uint32_t hist_len;      /* 1 + prime index of max_pmin */
+    uint32_t n_segments;    /* number of segments of seg_len even n */
+    uint32_t p_final;       /* largest bound used (P2 if a retry pass ran, else P) */
+    /* --- optional caller buffers (NULL = skip) --- */
+    uint64_t* hist;         /* host: hist[i] = #n whose p_min is the i-th
+                               prime, summed over the range; hist_cap entries;
+                               entries from hist_len on are written as 0 */
+    uint32_t  hist_cap;
+    uint32_t* pmin;         /* host or device: pmin[(n - lo)/2] = p_min(n), 0 if
+                               unresolved; n_checked entries */
+    gb_segment_result* segs;/* host or device: one record per segment, the
+                               first min(seg_cap, n_segments) are written
+                               (GB_ERANGE if seg_cap < n_segments) */
+    uint32_t  seg_cap;
+    uint64_t* seg_hist;     /* host or device: row k (seg_hist_stride entries)
+                               is segment k's histogram, rows for the first
+                               seg_cap segments (seg_cap 0: all n_segments
+                               rows); GB_ERANGE if a segment's hist_len exceeds
+                               the stride (the row is truncated) */
+    uint32_t  seg_hist_stride;
+    uint32_t  reserved;
+} gb_range_result;
+
+/* Create a context: select the device, sieve the base primes to
+ * cfg->base_limit on the GPU (the base sieve of Sec. 2.3.1), build the
+ * cover's prime tables to max(p1, p2).  cfg may be NULL (all defaults). */
+int gb_init(gb_ctx** out, const gb_config* cfg);
+
+/* Release every device resource of the context (NULL is a no-op). */
+void gb_destroy(gb_ctx* ctx);
+
+/* The configuration in effect, defaults filled in. */
+int gb_get_config(const gb_ctx* ctx, gb_config* out);
+
+/* Sieve one window of odd numbers (Sec. 2.2 layout, Sec. 2.3.1 segment sieve):
+ * bit i (bit i%64 of word i/64, little-endian bit order) of q_bits is 1 iff the
+ * odd number A_odd + 2i is prime, for 0 <= i < n_bits; bits from n_bits to the
+ * end of the last word are 0.  A_odd is odd and may be <= 1 (numbers below 2
+ * are not prime).  q_bits: DEVICE pointer, ceil(n_bits/64) uint64 words,
+ * 16-byte aligned.  popcount (host, may be NULL): number of 1 bits.
+ * GB_EINVAL if A_odd is even or A_odd + 2(n_bits-1) > base_limit^2. */
+int gb_sieve_segment(gb_ctx* ctx, int64_t A_odd, uint64_t n_bits,
+                     uint64_t* q_bits, uint64_t* popcount);
+
+/* pi(x): number of primes <= x, counted from GPU-sieved bitsets (x <=
+ * base_limit^2). */
+int gb_prime_pi(gb_ctx* ctx, uint64_t x, uint64_t* count);
+
+/* Exhaustive verification of every even n in [lo, hi) (Sec. 2.3, Table 4):
+ * p_min(n) for all n with p <= P (P = 0: the context's p1), then, if the
+ * context has p2 > P, a second GPU pass over the n still unresolved with
+ * P < p <= p2 (Sec. 2.3.3's fallback, moved to the GPU).  Results are exact
+ * integers.  Requires hi <= base_limit^2 and P <= 2^24. */
+int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P,
+                    gb_range_result* out);
+
+/* Per-kernel device time, measured with CUDA events recorded on the
+ * context's stream around every launch while profiling is enabled.  Kinds:
+ * 0 segment sieve (units: q bits sieved), 1 cover (units: even n), 2 retry
+ * pass (units: even n of the slabs it ran on), 3 reductions (units:
+ * segments).  gb_profile_enable resets the counters. */
+#define GB_PROF_KINDS 4
+int gb_profile_enable(gb_ctx* ctx, int enable);
+int gb_profile_read(gb_ctx* ctx, double* ms, uint64_t* launches, uint64_t* units);
+
+/* Work counted by the kernels while profiling is enabled: bits struck by the
+ * segment sieve (every strike of a prime >= 23, duplicates included), and the
+ * cover's word iterations, sum over 64-n words of the number of primes applied
+ * until the word filled (the bound's count for a word left open). */
+int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterations);
+
+/* Bytes of the odd-only dense bitset for the odd numbers 3..N (Sec. 2.2):
+ * ceil(#odd in [3, N] / 64) 64-bit words.  Host-only helper. */
+uint64_t gb_bitset_bytes(uint64_t N);
+
+/* Name of a GB_* code. */
+const char* gb_strerror(int code);
+
+/* Last error message of the calling thread ("" if none). */
+const char* gb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB_H */

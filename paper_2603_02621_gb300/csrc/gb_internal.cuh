@@ -1,0 +1,183 @@
+// gb_internal.cuh -- device helpers and kernel launchers shared by the
+// translation units of libgb (segment sieve, Goldbach cover, runtime).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gb {
+
+// ---------------------------------------------------------------------------
+// Wheel patterns for the primes 3..19 (pre-sieve stamp of the segment sieve).
+// Odd number v = 2x + 1 is divisible by the odd prime p iff x = (p-1)/2 mod p.
+// Pattern 1 covers {3,5,7,11,13} with period 15015 in x, pattern 2 covers
+// {17,19} with period 323; a tile word is the AND of both, read at x mod period.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kWheelM1 = 15015u;       // 3*5*7*11*13
+constexpr uint32_t kWheelM2 = 323u;         // 17*19
+constexpr uint32_t kWheelW1 = 472u;         // uint32 words holding bits [0, M1 + 64)
+constexpr uint32_t kWheelW2 = 13u;          // uint32 words holding bits [0, M2 + 64)
+constexpr uint32_t kFirstStrikeIdx = 8u;    // index of 23 in 2,3,5,7,11,13,17,19,23,...
+
+// Barrett reduction (P. Barrett, CRYPTO '86): with m = floor((2^64-1)/p), the
+// quotient estimate hi64(x*m) is at most 2 below floor(x/p); two conditional
+// subtractions finish the remainder.  p < 2^32, any 64-bit x.
+__device__ __forceinline__ uint32_t barrett_mod(uint64_t x, uint32_t p, uint64_t m)
+{
+    uint64_t q = __umul64hi(x, m);
+    uint64_t r = x - q * (uint64_t)p;
+    if (r >= p) r -= p;
+    if (r >= p) r -= p;
+    return (uint32_t)r;
+}
+
+// (-b) mod p in [0, p), b any signed 64-bit value
+__device__ __forceinline__ uint32_t neg_mod(int64_t b, uint32_t p, uint64_t m)
+{
+    if (b <= 0) return barrett_mod((uint64_t)(-b), p, m);
+    uint32_t t = barrett_mod((uint64_t)b, p, m);
+    return t ? p - t : 0u;
+}
+
+// Index i >= 0 of the first odd multiple of p in the odd-number sequence
+// b, b+2, b+4, ... (b odd): 2i = -b (mod p), i < p.
+__device__ __forceinline__ uint32_t first_odd_multiple(int64_t b, uint32_t p, uint64_t m)
+{
+    uint32_t r = neg_mod(b, p, m);
+    return (r & 1u) ? (uint32_t)(((uint64_t)r + p) >> 1) : (r >> 1);
+}
+
+// ---------------------------------------------------------------------------
+// Segment sieve
+// ---------------------------------------------------------------------------
+struct SieveArgs {
+    int64_t  B;                 // odd number of bit 0
+    uint64_t nbits;             // bits produced (a multiple of 64 is written per tile)
+    uint32_t tile_bits;         // bits per CTA tile (multiple of 8192)
+    const uint32_t* primes;     // sieving primes, ascending, starting at 23
+    const uint64_t* recip;      // Barrett reciprocals of the same primes
+    uint32_t n_warp;            // primes [0, n_warp): one warp strikes each
+    uint32_t n_primes;          // primes [n_warp, n_primes): one thread each
+    const uint32_t* wheel1;     // kWheelW1 words
+    const uint32_t* wheel2;     // kWheelW2 words
+    uint32_t* out;              // bit i -> word i/32, bit i%32 (NULL: count only)
+    unsigned long long* popcount;   // optional total of 1 bits
+    unsigned long long* strikes;    // optional: number of bits struck (work count)
+};
+
+cudaError_t launch_wheel_tables(uint32_t* w1, uint32_t* w2, cudaStream_t s);
+cudaError_t launch_seed_sieve(uint32_t* words /*1024*/, cudaStream_t s);
+cudaError_t launch_sieve(const SieveArgs& a, int threads, cudaStream_t s);
+
+// Compaction of an odd-only bitset (bit i <-> number B + 2i) into the list of
+// its primes, ascending, written after a leading 2; plus Barrett reciprocals.
+struct CompactArgs {
+    const uint32_t* words;
+    uint64_t nwords;
+    int64_t  B;
+    uint32_t* counts;           // scratch: one per chunk
+    uint32_t* primes;           // out: [2, odd primes...]
+    uint64_t* recip;            // out: floor((2^64-1)/p) per entry of primes
+};
+uint64_t compact_chunks(uint64_t nwords);
+cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Goldbach cover
+// ---------------------------------------------------------------------------
+struct RetryItem {
+    uint64_t w;                 // slab word index (64 even n per word)
+    uint64_t C;                 // coverage bits after the first pass
+};
+
+struct CoverArgs {
+    const uint64_t* Q;          // q window: bit i <-> odd number A0 - H + 1 + 2i
+    uint32_t H;                 // halo, even, > every p of the pass
+    uint64_t n_count;           // even n in the slab
+    uint64_t n_words;           // ceil(n_count / 64)
+    uint32_t words_per_seg;     // S / 64
+    uint32_t cta_words;         // words per CTA (multiple of 32)
+    uint32_t chunks_per_seg;    // ceil(words_per_seg / cta_words)
+    uint32_t nseg;              // segments in the slab
+    const uint32_t* primes;     // [2, 3, 5, ...]
+    uint32_t K;                 // odd primes used: primes[1 .. K]
+    uint32_t hist_stride;       // per-segment histogram row length
+    uint32_t* hist;             // [nseg][hist_stride], prime-index histogram
+    unsigned long long* maxkey; // [nseg]: (pidx+1) << 32 | (0xffffffff - j)
+    unsigned long long* unresolved; // [nseg]
+    uint32_t* pmin;             // optional, slab-relative n index
+    RetryItem* retry;           // optional: words left with zero bits go here
+    unsigned int* retry_count;
+    uint32_t retry_cap;
+    int has_n4;                 // slab starts at n = 4 (p_min(4) = 2)
+    unsigned long long* iters;  // optional: sum over words of the primes applied
+                                // until the word filled (work count)
+};
+cudaError_t launch_cover(const CoverArgs& a, int threads, cudaStream_t s);
+
+struct RetryArgs {
+    const uint64_t* Q;
+    uint32_t H;
+    uint32_t words_per_seg;
+    const uint32_t* primes;
+    uint32_t K1, K2;            // odd-prime indices (1-based in primes[]) K1 < k <= K2
+    uint32_t hist_stride;
+    uint32_t* hist;
+    unsigned long long* maxkey;
+    unsigned long long* unresolved;
+    uint32_t* pmin;
+    const RetryItem* items;
+    const unsigned int* count;
+    uint32_t cap;
+};
+cudaError_t launch_retry(const RetryArgs& a, cudaStream_t s);
+
+// Per-segment summary written by the reduce kernel (device layout, also the
+// staging layout copied to the host).
+struct SegSummary {
+    uint64_t unresolved;
+    uint64_t max_j;             // segment-relative n index of max_pmin
+    uint32_t max_pmin;
+    uint32_t hist_len;
+};
+
+struct ReduceArgs {
+    uint32_t nseg;
+    uint32_t hist_stride;
+    const uint32_t* hist;
+    const unsigned long long* maxkey;
+    const unsigned long long* unresolved;
+    const uint32_t* primes;
+    SegSummary* summary;        // [nseg]
+    uint64_t* rows;             // optional [nrows][row_stride] uint64 copy
+    uint32_t row_stride;
+    uint32_t nrows;             // rows written (<= nseg)
+    unsigned long long* merged; // [hist_stride] running sum over segments
+};
+cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s);
+
+// Totals over all segments of a range (device), and the public per-segment
+// records (gb_segment_result layout) written where the caller wants them.
+struct RangeTotals {
+    unsigned long long unresolved;
+    unsigned long long max_pmin_n;
+    uint32_t max_pmin;
+    uint32_t hist_len;
+};
+
+struct SegRecord {              // identical layout to gb_segment_result
+    uint64_t lo, hi, n_checked, unresolved, max_pmin_n;
+    uint32_t max_pmin, hist_len;
+};
+
+struct FinalizeArgs {
+    uint64_t lo, hi, S;
+    uint32_t nseg;
+    const SegSummary* summary;
+    SegRecord* records;         // optional
+    uint32_t nrecords;          // records written (<= nseg)
+    RangeTotals* totals;
+};
+cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+
+}  // namespace gb

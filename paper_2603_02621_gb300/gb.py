@@ -1,0 +1,267 @@
+"""Python binding of libgb (include/gb.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Device
+buffers may be given as torch CUDA tensors (their data pointer is passed) and
+host buffers as numpy arrays or torch CPU tensors; the stream is a
+``cudaStream_t`` handle (``torch.cuda.current_stream().cuda_stream``).  The
+library itself must be built (``python -m paper_2603_02621_gb300.build``): if
+``libgb.so`` is missing, loading fails loudly -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from ctypes import POINTER, c_char_p, c_int, c_int32, c_int64, c_uint32, c_uint64, c_void_p
+
+import numpy as np
+
+from .build import LIB
+
+GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ETIMEOUT, GB_EBUSY, GB_ERANGE = range(7)
+
+
+class GbError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail or 'error'} (code {code})")
+        self.code = code
+
+
+class gb_config(ctypes.Structure):
+    _fields_ = [("device", c_int32), ("seg_len", c_uint32), ("base_limit", c_uint64),
+                ("tile_bits", c_uint32), ("cta_threads", c_uint32), ("bucket_split", c_uint32),
+                ("p1", c_uint32), ("p2", c_uint32), ("slab_bits", c_uint64), ("stream", c_void_p)]
+
+
+class gb_segment_result(ctypes.Structure):
+    _fields_ = [("lo", c_uint64), ("hi", c_uint64), ("n_checked", c_uint64),
+                ("unresolved", c_uint64), ("max_pmin_n", c_uint64),
+                ("max_pmin", c_uint32), ("hist_len", c_uint32)]
+
+
+class gb_range_result(ctypes.Structure):
+    _fields_ = [("n_checked", c_uint64), ("unresolved", c_uint64), ("max_pmin_n", c_uint64),
+                ("max_pmin", c_uint32), ("hist_len", c_uint32), ("n_segments", c_uint32),
+                ("p_final", c_uint32),
+                ("hist", POINTER(c_uint64)), ("hist_cap", c_uint32),
+                ("pmin", c_void_p),
+                ("segs", POINTER(gb_segment_result)), ("seg_cap", c_uint32),
+                ("seg_hist", POINTER(c_uint64)), ("seg_hist_stride", c_uint32),
+                ("reserved", c_uint32)]
+
+
+# every exported entry point of include/gb.h, with its C signature
+SIGNATURES = {
+    "gb_init": (c_int, [POINTER(c_void_p), POINTER(gb_config)]),
+    "gb_destroy": (None, [c_void_p]),
+    "gb_get_config": (c_int, [c_void_p, POINTER(gb_config)]),
+    "gb_sieve_segment": (c_int, [c_void_p, c_int64, c_uint64, c_void_p, POINTER(c_uint64)]),
+    "gb_prime_pi": (c_int, [c_void_p, c_uint64, POINTER(c_uint64)]),
+    "gb_verify_range": (c_int, [c_void_p, c_uint64, c_uint64, c_uint32, POINTER(gb_range_result)]),
+    "gb_profile_enable": (c_int, [c_void_p, c_int]),
+    "gb_profile_read": (c_int, [c_void_p, POINTER(ctypes.c_double), POINTER(c_uint64), POINTER(c_uint64)]),
+    "gb_profile_work": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64)]),
+    "gb_bitset_bytes": (c_uint64, [c_uint64]),
+    "gb_strerror": (c_char_p, [c_int]),
+    "gb_last_error": (c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libgb.so (no fallback: a missing library is an error)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB
+        if not os.path.exists(p):
+            raise ImportError(f"libgb.so not built at {p}: run python -m paper_2603_02621_gb300.build")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str, allow=()):
+    if rc != GB_OK and rc not in allow:
+        lib = load()
+        raise GbError(rc, where, (lib.gb_last_error() or b"").decode() or lib.gb_strerror(rc).decode())
+    return rc
+
+
+def _ptr(buf) -> int:
+    """Raw address of a torch tensor, numpy array or int."""
+    if buf is None:
+        return 0
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        return int(buf.data_ptr())
+    if isinstance(buf, np.ndarray):
+        return int(buf.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def make_config(**kw) -> gb_config:
+    c = gb_config()
+    for k, v in kw.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = int(v.cuda_stream) if hasattr(v, "cuda_stream") else int(v)
+        setattr(c, k, v if v is not None else 0)
+    return c
+
+
+def gb_init(**kw) -> int:
+    lib = load()
+    cfg = make_config(**kw)
+    h = c_void_p()
+    _check(lib.gb_init(ctypes.byref(h), ctypes.byref(cfg)), "gb_init")
+    return h.value
+
+
+def gb_destroy(ctx: int) -> None:
+    if ctx:
+        load().gb_destroy(ctx)
+
+
+def gb_get_config(ctx: int) -> dict:
+    c = gb_config()
+    _check(load().gb_get_config(ctx, ctypes.byref(c)), "gb_get_config")
+    return {name: getattr(c, name) for name, _ in gb_config._fields_}
+
+
+def gb_sieve_segment(ctx: int, A_odd: int, n_bits: int, q_bits) -> int:
+    """Sieve odd numbers A_odd + 2i (i < n_bits) into the DEVICE buffer q_bits
+    (>= ceil(n_bits/64) uint64 words); returns the number of primes."""
+    pc = c_uint64()
+    _check(load().gb_sieve_segment(ctx, A_odd, n_bits, _ptr(q_bits), ctypes.byref(pc)),
+           "gb_sieve_segment")
+    return pc.value
+
+
+def gb_prime_pi(ctx: int, x: int) -> int:
+    c = c_uint64()
+    _check(load().gb_prime_pi(ctx, x, ctypes.byref(c)), "gb_prime_pi")
+    return c.value
+
+
+def gb_verify_range(ctx: int, lo: int, hi: int, P: int = 0, *, hist_cap: int = 0,
+                    pmin=None, segs: bool = False, seg_hist_stride: int = 0,
+                    allow_erange: bool = False) -> dict:
+    """Verify every even n in [lo, hi).  Returns a dict with the totals, and
+    'hist' (np.uint64[hist_cap]), 'segs' (structured rows), 'seg_hist'
+    (np.uint64[nseg, stride]) when asked.  pmin: optional uint32 buffer of
+    (hi-lo)/2 entries, host (numpy / CPU tensor) or device (CUDA tensor)."""
+    lib = load()
+    r = gb_range_result()
+    out = {}
+    S = gb_get_config(ctx)["seg_len"]
+    nseg = ((hi - lo) // 2 + S - 1) // S
+    hist = None
+    if hist_cap:
+        hist = np.zeros(hist_cap, dtype=np.uint64)
+        r.hist = hist.ctypes.data_as(POINTER(c_uint64))
+        r.hist_cap = hist_cap
+    if pmin is not None:
+        r.pmin = _ptr(pmin)
+    segarr = None
+    if segs or seg_hist_stride:
+        segarr = (gb_segment_result * nseg)()
+        r.segs = segarr
+        r.seg_cap = nseg
+    rows = None
+    if seg_hist_stride:
+        rows = np.zeros((nseg, seg_hist_stride), dtype=np.uint64)
+        r.seg_hist = rows.ctypes.data_as(POINTER(c_uint64))
+        r.seg_hist_stride = seg_hist_stride
+    rc = _check(lib.gb_verify_range(ctx, lo, hi, P, ctypes.byref(r)), "gb_verify_range",
+                allow=(GB_ERANGE,) if allow_erange else ())
+    out.update(rc=rc, n_checked=r.n_checked, unresolved=r.unresolved, max_pmin=r.max_pmin,
+               max_pmin_n=r.max_pmin_n, hist_len=r.hist_len, n_segments=r.n_segments,
+               p_final=r.p_final)
+    if hist is not None:
+        out["hist"] = hist
+    if segarr is not None:
+        out["segs"] = [dict(lo=s.lo, hi=s.hi, n_checked=s.n_checked, unresolved=s.unresolved,
+                            max_pmin=s.max_pmin, max_pmin_n=s.max_pmin_n, hist_len=s.hist_len)
+                       for s in segarr]
+    if rows is not None:
+        out["seg_hist"] = rows
+    return out
+
+
+GB_PROF_KINDS = 4
+PROF_NAMES = ("sieve", "cover", "retry", "reduce")
+
+
+def gb_profile_enable(ctx: int, enable: bool = True) -> None:
+    _check(load().gb_profile_enable(ctx, int(bool(enable))), "gb_profile_enable")
+
+
+def gb_profile_read(ctx: int) -> dict:
+    ms = (ctypes.c_double * GB_PROF_KINDS)()
+    ln = (c_uint64 * GB_PROF_KINDS)()
+    un = (c_uint64 * GB_PROF_KINDS)()
+    _check(load().gb_profile_read(ctx, ms, ln, un), "gb_profile_read")
+    return {PROF_NAMES[k]: dict(ms=ms[k], launches=ln[k], units=un[k]) for k in range(GB_PROF_KINDS)}
+
+
+def gb_profile_work(ctx: int) -> dict:
+    a, b = c_uint64(), c_uint64()
+    _check(load().gb_profile_work(ctx, ctypes.byref(a), ctypes.byref(b)), "gb_profile_work")
+    return dict(sieve_strikes=a.value, cover_iterations=b.value)
+
+
+def gb_bitset_bytes(N: int) -> int:
+    return int(load().gb_bitset_bytes(N))
+
+
+def gb_strerror(code: int) -> str:
+    return load().gb_strerror(code).decode()
+
+
+def gb_last_error() -> str:
+    return (load().gb_last_error() or b"").decode()
+
+
+class Context:
+    """Owning wrapper: ``with Context(base_limit=10**5) as g: g.verify_range(...)``."""
+
+    def __init__(self, **cfg):
+        self.handle = gb_init(**cfg)
+
+    def close(self):
+        if self.handle:
+            gb_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def config(self):
+        return gb_get_config(self.handle)
+
+    def sieve_segment(self, A_odd, n_bits, q_bits):
+        return gb_sieve_segment(self.handle, A_odd, n_bits, q_bits)
+
+    def prime_pi(self, x):
+        return gb_prime_pi(self.handle, x)
+
+    def verify_range(self, lo, hi, P=0, **kw):
+        return gb_verify_range(self.handle, lo, hi, P, **kw)
