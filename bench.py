@@ -198,6 +198,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lo", type=int, default=None, help="custom range start (profiling of smaller cases)")
+    ap.add_argument("--hi", type=int, default=None, help="custom range end")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -215,6 +217,8 @@ def main():
         backend_ready = True
     stream = torch.cuda.current_stream()
     lo, hi = rank_range(rank)
+    if args.lo is not None and args.hi is not None:
+        lo, hi = args.lo, args.hi
     base = max(10**5, math.isqrt(hi + 4096) + 1)
     ctx = gb.Context(device=local, base_limit=base, seg_len=SEG, p1=P1, p2=P2,
                      stream=stream.cuda_stream)

@@ -88,7 +88,7 @@ def test_sieve_rejects_even_base(ctx16, gbm):
 def test_sieve_rejects_beyond_base_limit(ctx16, gbm):
     q = torch.zeros(4, dtype=torch.int64, device="cuda")
     with pytest.raises(gbm.GbError):
-        ctx16.sieve_segment(2**33 + 1, 64, q)      # sqrt > 2^16 base primes
+        ctx16.sieve_segment(2**41 + 1, 64, q)      # sqrt beyond the 2^20 prime list
 
 
 @pytest.mark.parametrize("x,pi", [(int(a), int(b)) for a, b in read_golden("prime_counts.txt")])
@@ -239,4 +239,4 @@ def test_invalid_ranges(ctx16, gbm):
             ctx16.verify_range(lo, hi)
         assert e.value.code == gbm.GB_EINVAL
     with pytest.raises(gbm.GbError):
-        ctx16.verify_range(2**34, 2**34 + 10)     # sqrt beyond 2^20 primes
+        ctx16.verify_range(2**41, 2**41 + 10)     # sqrt beyond the 2^20 prime list
