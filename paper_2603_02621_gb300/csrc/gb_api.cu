@@ -13,6 +13,7 @@
 // two phases; the structure above keeps them and moves the sieve to the device.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -100,10 +101,11 @@ struct gb_ctx {
     DevBuf primes, recip;             // device copies
     DevBuf wheel1, wheel2;
     DevBuf q;                         // slab q window
-    DevBuf hist, maxkey, unres, retry, retry_count, summary, rows, merged, pmin, counter, totals, records;
+    DevBuf hist, maxkey, maxkey2, unres, retry, retry_count, summary, rows, merged, pmin, counter, totals, records;
     DevBuf work;                      // profiling work counters: [0] sieve strikes, [1] cover iterations
     uint64_t work_strikes = 0, work_iters = 0;
     int warp_split = 0;               // sieving primes below this strike one warp each
+    bool generic_cover = false;       // force the generic cover kernel (GB_COVER=generic)
 
     // per-kernel device time (CUDA events on the context's stream around each launch)
     bool profiling = false;
@@ -350,6 +352,7 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     ctx->stream = static_cast<cudaStream_t>(c.stream);
     ctx->L = std::max<uint64_t>({c.base_limit, c.p1, c.p2});
     ctx->warp_split = (int)(c.tile_bits / 64);
+    if (const char* e = getenv("GB_COVER")) ctx->generic_cover = std::string(e) == "generic";
     rc = build_primes(ctx);
     if (rc) {
         gb_destroy(ctx);
@@ -366,7 +369,7 @@ void gb_destroy(gb_ctx* ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->primes, &ctx->recip, &ctx->wheel1, &ctx->wheel2, &ctx->q, &ctx->hist,
-                      &ctx->maxkey, &ctx->unres, &ctx->retry, &ctx->retry_count, &ctx->summary,
+                      &ctx->maxkey, &ctx->maxkey2, &ctx->unres, &ctx->retry, &ctx->retry_count, &ctx->summary,
                       &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work};
     for (DevBuf* b : bufs) b->release();
     delete ctx;
@@ -438,7 +441,9 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
     const uint32_t Pf = retry ? cfg.p2 : P1;
     const uint32_t K1 = (uint32_t)(ctx->pi(P1) - 1);      // odd primes <= P1
     const uint32_t Kf = (uint32_t)(ctx->pi(Pf) - 1);
-    const uint32_t H = ((Pf + 1 + 127) / 128) * 128;      // halo: every p of both passes fits
+    // halo: larger than every p of both passes, and H = 4 (mod 64) so that the
+    // partner bits of p = 3 start on a 32-bit word boundary (two-phase cover)
+    const uint32_t H = 64 * ((Pf + 1 - 4 + 63) / 64) + 4;
     const uint64_t S = cfg.seg_len;
     const uint64_t n_total = (hi - lo) / 2;
     const uint64_t nseg = (n_total + S - 1) / S;
@@ -476,7 +481,8 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
     const uint32_t retry_cap = (uint32_t)std::min<uint64_t>(slab_words, 1u << 21);
     if ((rc = ctx->q.ensure(q_words * 8)) ||
         (rc = ctx->hist.ensure(slab_segs * hist_stride * 4)) ||
-        (rc = ctx->maxkey.ensure(slab_segs * 8)) || (rc = ctx->unres.ensure(slab_segs * 8)) ||
+        (rc = ctx->maxkey.ensure(slab_segs * 8)) || (rc = ctx->maxkey2.ensure(slab_segs * 8)) ||
+        (rc = ctx->unres.ensure(slab_segs * 8)) ||
         (retry && ((rc = ctx->retry.ensure((size_t)retry_cap * sizeof(gb::RetryItem))) ||
                    (rc = ctx->retry_count.ensure(8)))) ||
         (out->pmin && !pmin_dev && (rc = ctx->pmin.ensure(slab_n * 4))))
@@ -493,6 +499,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
 
         GB_CUDA(cudaMemsetAsync(ctx->hist.p, 0, ns * hist_stride * 4, s));
         GB_CUDA(cudaMemsetAsync(ctx->maxkey.p, 0, ns * 8, s));
+        GB_CUDA(cudaMemsetAsync(ctx->maxkey2.p, 0, ns * 8, s));
         GB_CUDA(cudaMemsetAsync(ctx->unres.p, 0, ns * 8, s));
         if (retry) GB_CUDA(cudaMemsetAsync(ctx->retry_count.p, 0, 8, s));
         uint32_t* pm = nullptr;
@@ -526,8 +533,12 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         ca.retry_cap = retry_cap;
         ca.has_n4 = (A0 == 4);
         ca.iters = ctx->work_ptr(1);
+        // two-phase kernel unless a p_min array is wanted (the generic kernel
+        // writes it) or the pass has too few primes for its first phase
+        const int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1);
         ctx->prof_begin(kProfCover, n_count);
-        GB_CUDA(gb::launch_cover(ca, (int)cfg.cta_threads, s));
+        if (KA) GB_CUDA(gb::launch_cover_fast(ca, KA, s));
+        else GB_CUDA(gb::launch_cover(ca, (int)cfg.cta_threads, s));
         ctx->prof_end();
 
         if (retry) {
@@ -551,8 +562,23 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
             ctx->prof_end();
         }
 
+        if (KA) {
+            // maxima of segments that neither the second phase nor the retry pass reached
+            gb::CoverArgs mx = ca;
+            mx.max_only = 1;
+            mx.maxkey_check = ca.maxkey;
+            mx.maxkey = ctx->maxkey2.as<unsigned long long>();
+            mx.pmin = nullptr;
+            mx.retry = nullptr;
+            mx.iters = nullptr;
+            ctx->prof_begin(kProfReduce, ns);
+            GB_CUDA(gb::launch_cover(mx, (int)cfg.cta_threads, s));
+            ctx->prof_end();
+        }
+
         gb::ReduceArgs rd{};
         rd.nseg = (uint32_t)ns;
+        rd.maxkey2 = KA ? ctx->maxkey2.as<unsigned long long>() : nullptr;
         rd.hist_stride = hist_stride;
         rd.hist = ca.hist;
         rd.maxkey = ca.maxkey;

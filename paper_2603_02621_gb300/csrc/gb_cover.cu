@@ -56,6 +56,10 @@ __global__ void __launch_bounds__(NT) k_cover(const CoverArgs a)
     if (w_end > seg_w0 + a.words_per_seg) w_end = seg_w0 + a.words_per_seg;
     if (w_end > a.n_words) w_end = a.n_words;
 
+    // max-only mode: only segments that no other pass gave a maximum
+    if (a.max_only && a.maxkey_check[seg] != 0) return;
+    const bool full = !a.max_only;
+
     for (uint32_t k = threadIdx.x; k < a.K; k += NT) sd[k] = (a.H - a.primes[1 + k] - 1) >> 1;
     for (uint32_t k = threadIdx.x; k <= a.K; k += NT) shist[k] = 0;
     if (threadIdx.x == 0) smax = 0;
@@ -63,6 +67,7 @@ __global__ void __launch_bounds__(NT) k_cover(const CoverArgs a)
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long best = 0;
+    uint32_t* const pmin = full ? a.pmin : nullptr;
 
     for (uint64_t wb = w_begin + 32 * warp; wb < w_end; wb += 32 * (NT / 32)) {
         const uint64_t w = wb + lane;
@@ -80,7 +85,7 @@ __global__ void __launch_bounds__(NT) k_cover(const CoverArgs a)
             last_pidx1 = 1;
             last_new = 1ull;
             atomicAdd(&shist[0], 1u);
-            if (a.pmin) a.pmin[0] = 2;
+            if (pmin) pmin[0] = 2;
         }
         const uint64_t* q = a.Q + w;
         for (uint32_t k = 0; k < a.K; ++k) {
@@ -97,20 +102,20 @@ __global__ void __launch_bounds__(NT) k_cover(const CoverArgs a)
             if (nw) {
                 last_pidx1 = k + 2;
                 last_new = nw;
-                if (a.pmin) {
+                if (pmin) {
                     const uint32_t p = a.primes[1 + k];
                     uint64_t m = nw;
                     while (m) {
                         const uint32_t bit = __ffsll(m) - 1;
                         m &= m - 1;
-                        a.pmin[64 * w + bit] = p;
+                        pmin[64 * w + bit] = p;
                     }
                 }
             }
             const uint32_t tot = __reduce_add_sync(0xffffffffu, c);
             if (lane == 0 && tot) atomicAdd(&shist[k + 1], tot);
         }
-        if (active && C != ~0ull) {
+        if (full && active && C != ~0ull) {
             bool queued = false;
             if (a.retry) {
                 const unsigned int slot = atomicAdd(a.retry_count, 1u);
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(NT) k_cover(const CoverArgs a)
             const unsigned long long key = ((unsigned long long)last_pidx1 << 32) | (0xffffffffull - j);
             if (key > best) best = key;
         }
-        if (a.iters) {
+        if (full && a.iters) {
             // primes applied until the word filled (all K when it did not)
             uint32_t it = active ? (C == ~0ull ? (last_pidx1 > 1 ? last_pidx1 - 1 : 0) : a.K) : 0;
             const uint32_t tot = __reduce_add_sync(0xffffffffu, it);
@@ -142,8 +147,9 @@ __global__ void __launch_bounds__(NT) k_cover(const CoverArgs a)
     if (lane == 0 && mhi) atomicMax(&smax, ((unsigned long long)mhi << 32) | mlo);
     __syncthreads();
     uint32_t* hrow = a.hist + (uint64_t)seg * a.hist_stride;
-    for (uint32_t k = threadIdx.x; k <= a.K; k += NT)
-        if (shist[k]) atomicAdd(&hrow[k], shist[k]);
+    if (full)
+        for (uint32_t k = threadIdx.x; k <= a.K; k += NT)
+            if (shist[k]) atomicAdd(&hrow[k], shist[k]);
     if (threadIdx.x == 0 && smax) atomicMax(&a.maxkey[seg], smax);
 }
 
@@ -228,7 +234,8 @@ cudaError_t launch_retry(const RetryArgs& a, cudaStream_t s)
 __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
 {
     const uint32_t seg = blockIdx.x;
-    const unsigned long long key = a.maxkey[seg];
+    unsigned long long key = a.maxkey[seg];
+    if (a.maxkey2 && a.maxkey2[seg] > key) key = a.maxkey2[seg];
     const uint32_t pidx1 = (uint32_t)(key >> 32);
     const uint32_t hl = pidx1;                      // entries >= hl are all zero
     const uint32_t* hrow = a.hist + (uint64_t)seg * a.hist_stride;

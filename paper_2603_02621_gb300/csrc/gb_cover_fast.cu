@@ -1,0 +1,283 @@
+// gb_cover_fast.cu -- two-phase form of the loop-inverted Goldbach cover.
+//
+// Same computation as the generic cover (gb_cover.cu): for p = 3, 5, 7, ... <= P
+// in ascending order, every even n whose partner n - p is prime and that no
+// smaller p covered gets p_min(n) = p (GoldbachGPU, arXiv 2603.02621, Sec.
+// 2.3.1-2.3.2, in the bitwise form of Sec. 4.3).  Only the schedule differs.
+//
+// Phase A.  Most n are covered by one of the first few dozen primes, so the
+// first KA odd primes are applied to every coverage word unconditionally, with
+// the loop unrolled at compile time.  A lane owns one 32-bit word of C (32 even
+// n).  With the halo chosen so that d_3 = (H - 4)/2 is a multiple of 32, the
+// partner bits of word w for the prime p start at bit 32(w + d_3/32) - (p-3)/2
+// of Q: the word offset and the shift of every step are compile-time constants,
+// and the few Q words a lane needs sit in registers.  A step is then
+//     s = funnel-shift of two window registers,  C |= s,  cum_k += popc(C)
+// and the histogram of the first phase follows from the cumulative counts:
+// #{n : p_min(n) = p_k} = cum_k - cum_{k-1}.
+//
+// Phase B.  The n still open after phase A (a few percent) are queued per warp
+// in shared memory and probed one by one: the bit of Q at j + d_k for k = KA,
+// KA+1, ... (four probes per step), the first set bit giving p_min.  Lanes that
+// finish take the next queued n, so the warp stays busy until the queue is
+// empty.  An n still open after K primes goes to the retry pass (or counts as
+// unresolved).
+//
+// The largest p_min of a segment, with its smallest n, comes from phase B (or
+// the retry pass).  A segment where no n needed more than KA primes gets its
+// maximum from the generic kernel run in max-only mode.
+#include <utility>
+
+#include "gb_internal.cuh"
+
+namespace gb {
+
+// k-th odd prime (k = 0 -> 3), evaluated at compile time
+__host__ __device__ constexpr uint32_t odd_prime(int k)
+{
+    uint32_t c = 1;
+    int n = -1;
+    while (n < k) {
+        c += 2;
+        bool prime = true;
+        for (uint32_t d = 3; d * d <= c; d += 2)
+            if (c % d == 0) { prime = false; break; }
+        if (prime) ++n;
+    }
+    return c;
+}
+
+// window registers needed for KA primes: R[t] = Q32[base - t], t <= (e+31)/32
+__host__ __device__ constexpr int window_regs(int KA)
+{
+    return (int)(((odd_prime(KA - 1) - 3) / 2 + 31) / 32) + 1;
+}
+
+template <int K, int NR, int KA>
+__device__ __forceinline__ void phase_a_step(const uint32_t (&R)[NR], uint32_t& C, uint32_t (&cum)[KA])
+{
+    constexpr uint32_t e = (odd_prime(K) - 3) / 2;    // bit distance from p = 3
+    constexpr uint32_t c = (e + 31) / 32;
+    constexpr uint32_t sh = 32 * c - e;
+    static_assert(c < (uint32_t)NR, "window too small");
+    uint32_t s;
+    if constexpr (sh == 0) s = R[c];
+    else s = __funnelshift_r(R[c], R[c - 1], sh);
+    C |= s;
+    cum[K] += __popc(C);
+}
+
+template <int NR, int KA, int... K>
+__device__ __forceinline__ void phase_a(std::integer_sequence<int, K...>, const uint32_t (&R)[NR], uint32_t& C,
+                                        uint32_t (&cum)[KA])
+{
+    (phase_a_step<K, NR, KA>(R, C, cum), ...);
+}
+
+constexpr int kQueueCap = 1024;      // queued n per warp (one round adds at most 1024)
+constexpr int kQueueRun = 256;       // start phase B once this many n wait
+
+// shared-memory layout (uint32 units): offsets table with 4 zero entries past
+// K (the 4-wide probes may read them; their results are masked), histogram
+__host__ __device__ constexpr uint32_t sd_len(uint32_t K) { return (K + 4 + 3) & ~3u; }
+__host__ __device__ constexpr uint32_t hist_len(uint32_t K) { return (K + 1 + 3) & ~3u; }
+
+template <int NT, int KA>
+__global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
+{
+    constexpr int NW = NT / 32;
+    constexpr int NR = window_regs(KA);
+    extern __shared__ uint32_t smem[];
+    uint32_t* sd = smem;                                    // d_k, K entries + 4 pad (0)
+    uint32_t* shist = sd + sd_len(a.K);                     // K + 1 counters
+    uint32_t* queues = shist + hist_len(a.K);               // NW * kQueueCap
+    __shared__ unsigned long long smax;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* queue = queues + warp * kQueueCap;
+
+    // this CTA's words (32-bit words of C, 32 even n each)
+    const uint64_t wps = 2ull * a.words_per_seg;
+    const uint32_t seg = blockIdx.x / a.chunks_per_seg;
+    const uint32_t chunk = blockIdx.x % a.chunks_per_seg;
+    const uint64_t seg_w0 = (uint64_t)seg * wps;
+    const uint64_t w_begin = seg_w0 + (uint64_t)chunk * (2ull * a.cta_words);
+    uint64_t w_end = w_begin + 2ull * a.cta_words;
+    const uint64_t n_words32 = (a.n_count + 31) / 32;
+    if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
+    if (w_end > n_words32) w_end = n_words32;
+
+    for (uint32_t k = threadIdx.x; k < sd_len(a.K); k += NT) sd[k] = k < a.K ? (a.H - a.primes[1 + k] - 1) >> 1 : 0u;
+    for (uint32_t k = threadIdx.x; k <= a.K; k += NT) shist[k] = 0;
+    if (threadIdx.x == 0) smax = 0;
+    __syncthreads();
+
+    const uint32_t* Qc = reinterpret_cast<const uint32_t*>(a.Q) + w_begin;   // CTA-relative words
+    const uint32_t D0w = ((a.H - 4) >> 1) >> 5;            // word offset of the p = 3 partner
+    const uint32_t j_cta = (uint32_t)(32 * (w_begin - seg_w0));   // segment-relative n of the CTA's first n
+
+    uint32_t cum[KA];
+#pragma unroll
+    for (int k = 0; k < KA; ++k) cum[k] = 0;
+    uint32_t init_pop = 0;
+    unsigned long long best = 0;
+    int qn = 0;                                             // warp-uniform queue length
+
+    // phase B over the queued n
+    auto drain = [&]() {
+        __syncwarp();
+        uint32_t next = 32;
+        int e = lane;
+        bool act = e < qn;
+        uint32_t rel = act ? queue[e] : 0u;
+        uint32_t k = KA;
+        while (__any_sync(0xffffffffu, act)) {
+            if (act) {
+                // probes k .. k+3 (sd is padded past K; probes beyond K are ignored)
+                uint32_t hit = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t i = rel + sd[k + t];
+                    hit |= ((__ldg(Qc + (i >> 5)) >> (i & 31)) & 1u) << t;
+                }
+                const uint32_t left = a.K - k;
+                if (left < 4) hit &= (1u << left) - 1u;
+                if (hit) {
+                    const uint32_t kk = k + (__ffs(hit) - 1);
+                    atomicAdd(&shist[kk + 1], 1u);
+                    const unsigned long long key =
+                        ((unsigned long long)(kk + 2) << 32) | (0xffffffffull - (j_cta + rel));
+                    if (key > best) best = key;
+                    act = false;
+                } else if (left <= 4) {
+                    // open after every prime of this pass
+                    const uint64_t jn = 32 * w_begin + rel;            // slab-relative n index
+                    bool queued = false;
+                    if (a.retry) {
+                        const unsigned int slot = atomicAdd(a.retry_count, 1u);
+                        if (slot < a.retry_cap) {
+                            a.retry[slot].w = jn >> 6;
+                            a.retry[slot].C = ~(1ull << (jn & 63));
+                            queued = true;
+                        }
+                    }
+                    if (!queued) atomicAdd(&a.unresolved[seg], 1ull);
+                    act = false;
+                } else {
+                    k += 4;
+                }
+            }
+            const unsigned idle = __ballot_sync(0xffffffffu, !act);
+            if (idle && next < (uint32_t)qn) {
+                const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
+                if (!act) {
+                    const uint32_t ne = next + rank;
+                    if (ne < (uint32_t)qn) {
+                        act = true;
+                        rel = queue[ne];
+                        k = KA;
+                    }
+                }
+                next += __popc(idle);
+            }
+        }
+        __syncwarp();
+        qn = 0;
+    };
+
+    for (uint64_t wb = w_begin + 32 * warp; wb < w_end; wb += 32 * NW) {
+        const uint64_t w = wb + lane;
+        const bool active = w < w_end;
+        const uint32_t wrel = (uint32_t)(w - w_begin);
+        uint32_t C = 0xffffffffu;
+        uint32_t R[NR];
+        if (active) {
+            C = 0;
+            const uint64_t j0 = 32 * w;
+            if (a.n_count - j0 < 32) C = 0xffffffffu << (a.n_count - j0);   // past the slab end
+            if (a.has_n4 && w == 0) {
+                C |= 1u;                                     // n = 4 = 2 + 2
+                atomicAdd(&shist[0], 1u);
+            }
+#pragma unroll
+            for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - t);
+        } else {
+#pragma unroll
+            for (int t = 0; t < NR; ++t) R[t] = 0;
+        }
+        init_pop += __popc(C);
+        phase_a<NR, KA>(std::make_integer_sequence<int, KA>{}, R, C, cum);
+
+        // queue the n still open
+        uint32_t m = ~C;
+        const uint32_t cnt = __popc(m);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (qn + (int)total > kQueueCap) drain();
+        uint32_t pos = qn + incl - cnt;
+        while (m) {
+            const uint32_t b = __ffs(m) - 1;
+            m &= m - 1;
+            queue[pos++] = (wrel << 5) | b;
+        }
+        qn += (int)total;
+        if (qn >= kQueueRun) drain();
+    }
+    if (qn) drain();
+
+    // first-phase histogram from the cumulative counts
+    uint32_t prev = __reduce_add_sync(0xffffffffu, init_pop);
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+        const uint32_t tot = __reduce_add_sync(0xffffffffu, cum[k]);
+        if (lane == 0 && tot != prev) atomicAdd(&shist[k + 1], tot - prev);
+        prev = tot;
+    }
+    // second-phase maximum: warp, CTA, segment
+    const uint32_t khi = (uint32_t)(best >> 32);
+    const uint32_t mhi = __reduce_max_sync(0xffffffffu, khi);
+    const uint32_t klo = khi == mhi ? (uint32_t)best : 0u;
+    const uint32_t mlo = __reduce_max_sync(0xffffffffu, klo);
+    if (lane == 0 && mhi) atomicMax(&smax, ((unsigned long long)mhi << 32) | mlo);
+    __syncthreads();
+    uint32_t* hrow = a.hist + (uint64_t)seg * a.hist_stride;
+    for (uint32_t k = threadIdx.x; k <= a.K; k += NT)
+        if (shist[k]) atomicAdd(&hrow[k], shist[k]);
+    if (threadIdx.x == 0 && smax) atomicMax(&a.maxkey[seg], smax);
+}
+
+int cover_fast_phase_primes(uint32_t K)
+{
+    if (K >= 64) return 64;
+    if (K >= 32) return 32;
+    return 0;
+}
+
+template <int KA>
+static cudaError_t launch_ka(const CoverArgs& a, cudaStream_t s)
+{
+    constexpr int NT = 256;
+    const unsigned grid = a.nseg * a.chunks_per_seg;
+    if (grid == 0) return cudaSuccess;
+    const size_t smem = (size_t)(sd_len(a.K) + hist_len(a.K) + (NT / 32) * kQueueCap) * 4;
+    auto k = k_cover_fast<NT, KA>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s)
+{
+    switch (KA) {
+    case 32: return launch_ka<32>(a, s);
+    case 64: return launch_ka<64>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gb

@@ -112,8 +112,20 @@ struct CoverArgs {
     int has_n4;                 // slab starts at n = 4 (p_min(4) = 2)
     unsigned long long* iters;  // optional: sum over words of the primes applied
                                 // until the word filled (work count)
+    // generic kernel only: "max only" mode recomputes the segment maximum of
+    // segments whose key in maxkey_check is still 0 and writes it to maxkey
+    int max_only;
+    const unsigned long long* maxkey_check;
 };
 cudaError_t launch_cover(const CoverArgs& a, int threads, cudaStream_t s);
+
+// Two-phase cover: an unrolled first phase over the first KA odd primes on
+// 32-bit coverage words, then per-n probing of the n still open (up to K).
+// Needs K >= KA, H = 4 (mod 64) and no p_min array; does not record the
+// maximum of words closed in the first phase (the generic kernel in max-only
+// mode fills it in for segments where nothing else set a key).
+int cover_fast_phase_primes(uint32_t K);        // KA to use for K primes (0: none)
+cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s);
 
 struct RetryArgs {
     const uint64_t* Q;
@@ -146,6 +158,7 @@ struct ReduceArgs {
     uint32_t hist_stride;
     const uint32_t* hist;
     const unsigned long long* maxkey;
+    const unsigned long long* maxkey2;  // optional second key per segment (max-only pass)
     const unsigned long long* unresolved;
     const uint32_t* primes;
     SegSummary* summary;        // [nseg]

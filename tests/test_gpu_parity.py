@@ -156,6 +156,62 @@ def test_edge_ranges(ctx16, oracle, lo, hi):
     assert np.array_equal(r["seg_hist"], hist)
 
 
+@pytest.mark.parametrize("lo,hi", [
+    (4, 6), (6, 8), (4, 130), (4, 4098), (10**9 + 2, 10**9 + 4),
+    (10**9 + 2, 10**9 + 2 + 2 * 4095), (2**40, 2**40 + 2 * 3001),
+    (4, 2 * (1 << 16) * 3 + 4 + 2 * 77),
+    (10**12 + 10, 10**12 + 10 + 2 * 300007),
+])
+def test_edge_ranges_two_phase(ctx16, oracle, lo, hi):
+    """Without a p_min array the two-phase cover kernel runs; same outputs."""
+    P2 = 1 << 20
+    H = hist_len_for(oracle, 1 << 15)
+    r = ctx16.verify_range(lo, hi, seg_hist_stride=H, hist_cap=H)
+    summ, hist = oracle.verify_segments(lo, hi, 1 << 16, P2, H)
+    got = np.array([[s["n_checked"], s["unresolved"], s["max_pmin"], s["max_pmin_n"]]
+                    for s in r["segs"]], dtype=np.uint64)
+    assert np.array_equal(got, summ)
+    assert np.array_equal(r["seg_hist"], hist)
+    assert np.array_equal(r["hist"], hist.sum(axis=0))
+
+
+def test_two_phase_into_retry(gbm, oracle):
+    """P1 = 2^8 (53 odd primes: first phase of 32, second phase to 256), retry
+    to 2^16: n with p_min > 256 travel through all three stages."""
+    lo, hi = 10**9, 10**9 + 2 * 2 * 10**6
+    H = hist_len_for(oracle, 1 << 16)
+    with gbm.Context(device=0, base_limit=1 << 16, seg_len=1 << 18, p1=1 << 8, p2=1 << 16) as g:
+        r = g.verify_range(lo, hi, seg_hist_stride=H, hist_cap=H)
+    summ, hist = oracle.verify_segments(lo, hi, 1 << 18, 1 << 16, H)
+    assert hist[:, 55:].sum() > 0                       # some p_min above 2^8 exist
+    got = np.array([[s["n_checked"], s["unresolved"], s["max_pmin"], s["max_pmin_n"]]
+                    for s in r["segs"]], dtype=np.uint64)
+    assert np.array_equal(got, summ)
+    assert np.array_equal(r["seg_hist"], hist)
+
+
+def test_two_phase_without_retry_counts_unresolved(gbm, oracle):
+    lo, hi = 10**9, 10**9 + 2 * 10**6
+    with gbm.Context(device=0, base_limit=1 << 16, seg_len=1 << 18, p1=1 << 8) as g:
+        r = g.verify_range(lo, hi, segs=True)
+    ref = oracle.pmin_range(lo, hi, 1 << 8)
+    assert r["unresolved"] == int((ref == 0).sum()) > 0
+    assert r["max_pmin"] == int(ref.max())
+
+
+def test_two_phase_matches_generic(gbm, monkeypatch):
+    """The two-phase and the generic cover kernels give identical results."""
+    lo, hi = 3 * 10**11, 3 * 10**11 + 2 * 5 * 10**6
+    base = dict(device=0, base_limit=1 << 20, seg_len=1 << 20, p1=1 << 15, p2=1 << 20)
+    with gbm.Context(**base) as g:
+        a = g.verify_range(lo, hi, seg_hist_stride=3512, hist_cap=3512)
+    monkeypatch.setenv("GB_COVER", "generic")
+    with gbm.Context(**base) as g:
+        b = g.verify_range(lo, hi, seg_hist_stride=3512, hist_cap=3512)
+    assert a["segs"] == b["segs"]
+    assert np.array_equal(a["seg_hist"], b["seg_hist"])
+
+
 def test_n4_histogram_entry(ctx16):
     r = ctx16.verify_range(4, 6, hist_cap=4)
     assert r["max_pmin"] == 2 and r["max_pmin_n"] == 4
