@@ -99,7 +99,7 @@ struct gb_ctx {
     uint64_t L = 0;                   // primes are known up to L
     std::vector<uint32_t> h_primes;   // [2, 3, 5, ...] <= L
     DevBuf primes, recip;             // device copies
-    DevBuf wheel1, wheel2;
+    DevBuf wheel;                     // pre-sieve stamp tables
     DevBuf q;                         // slab q window
     DevBuf hist, maxkey, maxkey2, unres, retry, retry_count, summary, rows, merged, pmin, counter, totals, records;
     DevBuf work;                      // profiling work counters: [0] sieve strikes, [1] cover iterations
@@ -221,8 +221,7 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
                                                             ? ctx->pi((uint64_t)ctx->warp_split - 1) - gb::kFirstStrikeIdx : 0);
     a.n_warp = (uint32_t)nwarp;
     a.n_primes = (uint32_t)nstrike;
-    a.wheel1 = ctx->wheel1.as<uint32_t>();
-    a.wheel2 = ctx->wheel2.as<uint32_t>();
+    a.wheel = ctx->wheel.as<uint32_t>();
     a.out = out;
     a.popcount = popc;
     a.strikes = ctx->work_ptr(0);
@@ -234,8 +233,8 @@ int build_primes(gb_ctx* ctx)
 {
     cudaStream_t s = ctx->stream;
     int rc;
-    if ((rc = ctx->wheel1.ensure(gb::kWheelW1 * 4)) || (rc = ctx->wheel2.ensure(gb::kWheelW2 * 4))) return rc;
-    GB_CUDA(gb::launch_wheel_tables(ctx->wheel1.as<uint32_t>(), ctx->wheel2.as<uint32_t>(), s));
+    if ((rc = ctx->wheel.ensure(gb::kWheelWords * 4))) return rc;
+    GB_CUDA(gb::launch_wheel_tables(ctx->wheel.as<uint32_t>(), s));
 
     // seed: odd numbers 1 .. 65535
     DevBuf seedbits, counts, seedp, seedr;
@@ -368,7 +367,7 @@ void gb_destroy(gb_ctx* ctx)
     cudaSetDevice(ctx->cfg.device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&ctx->primes, &ctx->recip, &ctx->wheel1, &ctx->wheel2, &ctx->q, &ctx->hist,
+    DevBuf* bufs[] = {&ctx->primes, &ctx->recip, &ctx->wheel, &ctx->q, &ctx->hist,
                       &ctx->maxkey, &ctx->maxkey2, &ctx->unres, &ctx->retry, &ctx->retry_count, &ctx->summary,
                       &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work};
     for (DevBuf* b : bufs) b->release();
@@ -535,7 +534,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         ca.iters = ctx->work_ptr(1);
         // two-phase kernel unless a p_min array is wanted (the generic kernel
         // writes it) or the pass has too few primes for its first phase
-        const int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1);
+        const int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
         ctx->prof_begin(kProfCover, n_count);
         if (KA) GB_CUDA(gb::launch_cover_fast(ca, KA, s));
         else GB_CUDA(gb::launch_cover(ca, (int)cfg.cta_threads, s));

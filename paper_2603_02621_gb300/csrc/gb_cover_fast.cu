@@ -53,8 +53,11 @@ __host__ __device__ constexpr int window_regs(int KA)
     return (int)(((odd_prime(KA - 1) - 3) / 2 + 31) / 32) + 1;
 }
 
-template <int K, int NR, int KA>
-__device__ __forceinline__ void phase_a_step(const uint32_t (&R)[NR], uint32_t& C, uint32_t (&cum)[KA])
+// cumulative counts are kept two per register (16-bit halves): a lane adds at
+// most 32 per word and handles fewer than 64 words per CTA (2047 * 32 < 2^16)
+
+template <int K, int NR, int KH>
+__device__ __forceinline__ void phase_a_step(const uint32_t (&R)[NR], uint32_t& C, uint32_t (&cum)[KH])
 {
     constexpr uint32_t e = (odd_prime(K) - 3) / 2;    // bit distance from p = 3
     constexpr uint32_t c = (e + 31) / 32;
@@ -64,18 +67,19 @@ __device__ __forceinline__ void phase_a_step(const uint32_t (&R)[NR], uint32_t& 
     if constexpr (sh == 0) s = R[c];
     else s = __funnelshift_r(R[c], R[c - 1], sh);
     C |= s;
-    cum[K] += __popc(C);
+    if constexpr (K & 1) cum[K >> 1] += __popc(C) << 16;
+    else cum[K >> 1] += __popc(C);
 }
 
-template <int NR, int KA, int... K>
+template <int NR, int KH, int... K>
 __device__ __forceinline__ void phase_a(std::integer_sequence<int, K...>, const uint32_t (&R)[NR], uint32_t& C,
-                                        uint32_t (&cum)[KA])
+                                        uint32_t (&cum)[KH])
 {
-    (phase_a_step<K, NR, KA>(R, C, cum), ...);
+    (phase_a_step<K, NR, KH>(R, C, cum), ...);
 }
 
 constexpr int kQueueCap = 1024;      // queued n per warp (one round adds at most 1024)
-constexpr int kQueueRun = 256;       // start phase B once this many n wait
+constexpr int kQueueRun = 192;       // start phase B once this many n wait
 
 // shared-memory layout (uint32 units): offsets table with 4 zero entries past
 // K (the 4-wide probes may read them; their results are masked), histogram
@@ -90,11 +94,13 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
     extern __shared__ uint32_t smem[];
     uint32_t* sd = smem;                                    // d_k, K entries + 4 pad (0)
     uint32_t* shist = sd + sd_len(a.K);                     // K + 1 counters
-    uint32_t* queues = shist + hist_len(a.K);               // NW * kQueueCap
+    uint16_t* queues = reinterpret_cast<uint16_t*>(shist + hist_len(a.K));   // NW * kQueueCap
     __shared__ unsigned long long smax;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* queue = queues + warp * kQueueCap;
+    // queue entry: round << 10 | lane << 5 | bit, i.e. the n at CTA-relative
+    // index 32 * (32 * (NW * round + warp) + lane) + bit
+    uint16_t* queue = queues + warp * kQueueCap;
 
     // this CTA's words (32-bit words of C, 32 even n each)
     const uint64_t wps = 2ull * a.words_per_seg;
@@ -116,9 +122,10 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
     const uint32_t D0w = ((a.H - 4) >> 1) >> 5;            // word offset of the p = 3 partner
     const uint32_t j_cta = (uint32_t)(32 * (w_begin - seg_w0));   // segment-relative n of the CTA's first n
 
-    uint32_t cum[KA];
+    constexpr int KH = KA / 2;
+    uint32_t cum[KH];
 #pragma unroll
-    for (int k = 0; k < KA; ++k) cum[k] = 0;
+    for (int k = 0; k < KH; ++k) cum[k] = 0;
     uint32_t init_pop = 0;
     unsigned long long best = 0;
     int qn = 0;                                             // warp-uniform queue length
@@ -127,9 +134,12 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
     auto drain = [&]() {
         __syncwarp();
         uint32_t next = 32;
+        auto decode = [&](uint32_t q) {
+            return ((((q >> 10) * NW + warp) * 32 + ((q >> 5) & 31)) << 5) | (q & 31);
+        };
         int e = lane;
         bool act = e < qn;
-        uint32_t rel = act ? queue[e] : 0u;
+        uint32_t rel = act ? decode(queue[e]) : 0u;
         uint32_t k = KA;
         while (__any_sync(0xffffffffu, act)) {
             if (act) {
@@ -174,7 +184,7 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
                     const uint32_t ne = next + rank;
                     if (ne < (uint32_t)qn) {
                         act = true;
-                        rel = queue[ne];
+                        rel = decode(queue[ne]);
                         k = KA;
                     }
                 }
@@ -185,7 +195,8 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
         qn = 0;
     };
 
-    for (uint64_t wb = w_begin + 32 * warp; wb < w_end; wb += 32 * NW) {
+    uint32_t round = 0;
+    for (uint64_t wb = w_begin + 32 * warp; wb < w_end; wb += 32 * NW, ++round) {
         const uint64_t w = wb + lane;
         const bool active = w < w_end;
         const uint32_t wrel = (uint32_t)(w - w_begin);
@@ -206,10 +217,11 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
             for (int t = 0; t < NR; ++t) R[t] = 0;
         }
         init_pop += __popc(C);
-        phase_a<NR, KA>(std::make_integer_sequence<int, KA>{}, R, C, cum);
+        phase_a<NR, KH>(std::make_integer_sequence<int, KA>{}, R, C, cum);
 
         // queue the n still open
         uint32_t m = ~C;
+        if (!__any_sync(0xffffffffu, m != 0)) continue;
         const uint32_t cnt = __popc(m);
         uint32_t incl = cnt;
 #pragma unroll
@@ -220,10 +232,11 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         if (qn + (int)total > kQueueCap) drain();
         uint32_t pos = qn + incl - cnt;
+        const uint32_t tag = (round << 10) | ((uint32_t)lane << 5);
         while (m) {
             const uint32_t b = __ffs(m) - 1;
             m &= m - 1;
-            queue[pos++] = (wrel << 5) | b;
+            queue[pos++] = (uint16_t)(tag | b);
         }
         qn += (int)total;
         if (qn >= kQueueRun) drain();
@@ -234,7 +247,8 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
     uint32_t prev = __reduce_add_sync(0xffffffffu, init_pop);
 #pragma unroll
     for (int k = 0; k < KA; ++k) {
-        const uint32_t tot = __reduce_add_sync(0xffffffffu, cum[k]);
+        const uint32_t v = (k & 1) ? cum[k >> 1] >> 16 : cum[k >> 1] & 0xffffu;
+        const uint32_t tot = __reduce_add_sync(0xffffffffu, v);
         if (lane == 0 && tot != prev) atomicAdd(&shist[k + 1], tot - prev);
         prev = tot;
     }
@@ -251,10 +265,16 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
     if (threadIdx.x == 0 && smax) atomicMax(&a.maxkey[seg], smax);
 }
 
-int cover_fast_phase_primes(uint32_t K)
+int cover_fast_phase_primes(uint32_t K, uint64_t n_hi)
 {
-    if (K >= 64) return 64;
-    if (K >= 32) return 32;
+    // first-phase length by magnitude: the share of n still open after KA
+    // primes grows with log n (about 0.6% after 64 primes near 1e10, 0.6%
+    // after 128 near 4e18), and a second-phase probe costs several first-phase
+    // steps' worth of work per n
+    int want = n_hi < 1000000000ull ? 48 : n_hi < 100000000000ull ? 64 : n_hi < 100000000000000ull ? 96 : 128;
+    const int opts[5] = {128, 96, 64, 48, 32};
+    for (int o : opts)
+        if (o <= want && (uint32_t)o <= K) return o;
     return 0;
 }
 
@@ -264,7 +284,7 @@ static cudaError_t launch_ka(const CoverArgs& a, cudaStream_t s)
     constexpr int NT = 256;
     const unsigned grid = a.nseg * a.chunks_per_seg;
     if (grid == 0) return cudaSuccess;
-    const size_t smem = (size_t)(sd_len(a.K) + hist_len(a.K) + (NT / 32) * kQueueCap) * 4;
+    const size_t smem = (size_t)(sd_len(a.K) + hist_len(a.K)) * 4 + (size_t)(NT / 32) * kQueueCap * 2;
     auto k = k_cover_fast<NT, KA>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<grid, NT, smem, s>>>(a);
@@ -273,9 +293,14 @@ static cudaError_t launch_ka(const CoverArgs& a, cudaStream_t s)
 
 cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s)
 {
+    // 16-bit queue entries hold rounds < 64; 16-bit counters hold a lane's sum
+    if (2ull * a.cta_words > 64ull * 256) return cudaErrorInvalidValue;
     switch (KA) {
     case 32: return launch_ka<32>(a, s);
+    case 48: return launch_ka<48>(a, s);
     case 64: return launch_ka<64>(a, s);
+    case 96: return launch_ka<96>(a, s);
+    case 128: return launch_ka<128>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -8,16 +8,23 @@
 namespace gb {
 
 // ---------------------------------------------------------------------------
-// Wheel patterns for the primes 3..19 (pre-sieve stamp of the segment sieve).
+// Pre-sieve patterns for the primes 3..43 (stamp of the segment sieve).
 // Odd number v = 2x + 1 is divisible by the odd prime p iff x = (p-1)/2 mod p.
-// Pattern 1 covers {3,5,7,11,13} with period 15015 in x, pattern 2 covers
-// {17,19} with period 323; a tile word is the AND of both, read at x mod period.
+// Four periodic patterns over x: {3,5,7,11,13} (period 15015), {17,19} (323),
+// {23,29,31} (20677) and {37,41,43} (65231); a tile word is the AND of the four,
+// each read at x mod its period.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kWheelM1 = 15015u;       // 3*5*7*11*13
 constexpr uint32_t kWheelM2 = 323u;         // 17*19
+constexpr uint32_t kWheelM3 = 20677u;       // 23*29*31
+constexpr uint32_t kWheelM4 = 65231u;       // 37*41*43
 constexpr uint32_t kWheelW1 = 472u;         // uint32 words holding bits [0, M1 + 64)
 constexpr uint32_t kWheelW2 = 13u;          // uint32 words holding bits [0, M2 + 64)
-constexpr uint32_t kFirstStrikeIdx = 8u;    // index of 23 in 2,3,5,7,11,13,17,19,23,...
+constexpr uint32_t kWheelW3 = 650u;         // uint32 words holding bits [0, M3 + 64)
+constexpr uint32_t kWheelW4 = 2042u;        // uint32 words holding bits [0, M4 + 64)
+constexpr uint32_t kWheelWords = kWheelW1 + kWheelW2 + kWheelW3 + kWheelW4;   // 3177, +3 pad
+constexpr uint32_t kStampedPrimes = 14u;    // 3 .. 43 come from the stamp
+constexpr uint32_t kFirstStrikeIdx = 14u;   // index of 47 in 2,3,5,7,...,43,47,...
 
 // Barrett reduction (P. Barrett, CRYPTO '86): with m = floor((2^64-1)/p), the
 // quotient estimate hi64(x*m) is at most 2 below floor(x/p); two conditional
@@ -58,14 +65,13 @@ struct SieveArgs {
     const uint64_t* recip;      // Barrett reciprocals of the same primes
     uint32_t n_warp;            // primes [0, n_warp): one warp strikes each
     uint32_t n_primes;          // primes [n_warp, n_primes): one thread each
-    const uint32_t* wheel1;     // kWheelW1 words
-    const uint32_t* wheel2;     // kWheelW2 words
+    const uint32_t* wheel;      // the four stamp tables, kWheelWords words
     uint32_t* out;              // bit i -> word i/32, bit i%32 (NULL: count only)
     unsigned long long* popcount;   // optional total of 1 bits
     unsigned long long* strikes;    // optional: number of bits struck (work count)
 };
 
-cudaError_t launch_wheel_tables(uint32_t* w1, uint32_t* w2, cudaStream_t s);
+cudaError_t launch_wheel_tables(uint32_t* wheel /*kWheelWords*/, cudaStream_t s);
 cudaError_t launch_seed_sieve(uint32_t* words /*1024*/, cudaStream_t s);
 cudaError_t launch_sieve(const SieveArgs& a, int threads, cudaStream_t s);
 
@@ -124,7 +130,7 @@ cudaError_t launch_cover(const CoverArgs& a, int threads, cudaStream_t s);
 // Needs K >= KA, H = 4 (mod 64) and no p_min array; does not record the
 // maximum of words closed in the first phase (the generic kernel in max-only
 // mode fills it in for segments where nothing else set a key).
-int cover_fast_phase_primes(uint32_t K);        // KA to use for K primes (0: none)
+int cover_fast_phase_primes(uint32_t K, uint64_t n_hi);   // KA for K primes near n_hi (0: none)
 cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s);
 
 struct RetryArgs {

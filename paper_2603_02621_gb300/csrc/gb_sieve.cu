@@ -8,10 +8,10 @@
 //   * the bit layout is the dense odd-only bitset of Sec. 2.2 (one bit per odd
 //     number, 64-bit words, little-endian bit order), with bit 0 at a chosen odd
 //     base instead of 3;
-//   * one CTA owns one tile of the window in shared memory: the wheel primes
-//     3..19 are stamped from two periodic patterns, primes 23 <= p strike
-//     their odd multiples from max(p^2, tile start) with shared-memory
-//     atomicAnd (one warp per small prime, one thread per larger prime), and the
+//   * one CTA owns one tile of the window in shared memory: the primes 3..43
+//     are stamped from four periodic patterns, primes 47 <= p strike their
+//     odd multiples from max(p^2, tile start) with shared-memory atomicAnd
+//     (one warp per small prime, one thread per larger prime), and the
 //     finished tile is stored with coalesced writes;
 //   * the first multiple of p in a tile comes from a Barrett remainder with a
 //     per-prime reciprocal, so no 64-bit division runs in the hot loop.
@@ -20,39 +20,32 @@
 namespace gb {
 
 // ---------------------------------------------------------------------------
-// wheel tables: bit x (x = 0 .. 32*words-1) is 1 iff no prime of the table
-// divides 2x + 1, i.e. x mod p != (p-1)/2 for each p.
+// stamp tables: in table t, bit x (x = 0 .. 32*words-1) is 1 iff no prime of
+// the table divides 2x + 1, i.e. x mod p != (p-1)/2 for each of its primes
 // ---------------------------------------------------------------------------
-__global__ void k_wheel_tables(uint32_t* w1, uint32_t* w2)
+__global__ void k_wheel_tables(uint32_t* wheel)
 {
-    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t P1[5] = {3, 5, 7, 11, 13};
-    const uint32_t P2[2] = {17, 19};
-    if (t < kWheelW1) {
-        uint32_t v = 0;
-        for (uint32_t b = 0; b < 32; ++b) {
-            uint32_t x = 32 * t + b;
-            bool keep = true;
-            for (int k = 0; k < 5; ++k) keep &= (x % P1[k]) != (P1[k] - 1) / 2;
-            v |= (uint32_t)keep << b;
-        }
-        w1[t] = v;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t P[14] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 0};
+    const uint32_t first[5] = {0, 5, 7, 10, 13};                 // primes of table i: P[first[i] .. first[i+1])
+    const uint32_t base[5] = {0, kWheelW1, kWheelW1 + kWheelW2, kWheelW1 + kWheelW2 + kWheelW3, kWheelWords};
+    if (t >= kWheelWords) return;
+    int tab = 0;
+    while (t >= base[tab + 1]) ++tab;
+    const uint32_t wi = t - base[tab];
+    uint32_t v = 0;
+    for (uint32_t b = 0; b < 32; ++b) {
+        const uint32_t x = 32 * wi + b;
+        bool keep = true;
+        for (uint32_t k = first[tab]; k < first[tab + 1]; ++k) keep &= (x % P[k]) != (P[k] - 1) / 2;
+        v |= (uint32_t)keep << b;
     }
-    if (t < kWheelW2) {
-        uint32_t v = 0;
-        for (uint32_t b = 0; b < 32; ++b) {
-            uint32_t x = 32 * t + b;
-            bool keep = true;
-            for (int k = 0; k < 2; ++k) keep &= (x % P2[k]) != (P2[k] - 1) / 2;
-            v |= (uint32_t)keep << b;
-        }
-        w2[t] = v;
-    }
+    wheel[t] = v;
 }
 
-cudaError_t launch_wheel_tables(uint32_t* w1, uint32_t* w2, cudaStream_t s)
+cudaError_t launch_wheel_tables(uint32_t* wheel, cudaStream_t s)
 {
-    k_wheel_tables<<<(kWheelW1 + 255) / 256, 256, 0, s>>>(w1, w2);
+    k_wheel_tables<<<(kWheelWords + 255) / 256, 256, 0, s>>>(wheel);
     return cudaGetLastError();
 }
 
@@ -96,13 +89,23 @@ __device__ __forceinline__ uint32_t pmod_u32(int64_t x, uint32_t M)
     return (uint32_t)(r < 0 ? r + M : r);
 }
 
+// one stamp table read at pattern offset a (a < period): 32 bits from bit a
+__device__ __forceinline__ uint32_t stamp_word(const uint32_t* tab, uint32_t a)
+{
+    return __funnelshift_r(tab[a >> 5], tab[(a >> 5) + 1], a & 31);
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_sieve(const SieveArgs a)
 {
+    constexpr int NW = NT / 32;
     extern __shared__ uint32_t smem[];
-    uint32_t* w1 = smem;                              // kWheelW1
-    uint32_t* w2 = smem + kWheelW1;                   // kWheelW2 (+3 pad)
-    uint32_t* sm = smem + kWheelW1 + kWheelW2 + 3;    // tile words (16B aligned)
+    uint32_t* wt = smem;                              // stamp tables (kWheelWords + 3 pad)
+    uint32_t* sm = smem + kWheelWords + 3;            // tile words (16B aligned)
+    const uint32_t* w1 = wt;
+    const uint32_t* w2 = w1 + kWheelW1;
+    const uint32_t* w3 = w2 + kWheelW2;
+    const uint32_t* w4 = w3 + kWheelW3;
 
     const uint64_t t0 = (uint64_t)blockIdx.x * a.tile_bits;
     const uint64_t rem = a.nbits - t0;
@@ -110,53 +113,78 @@ __global__ void __launch_bounds__(NT) k_sieve(const SieveArgs a)
     const uint32_t nw = ((nb + 63) / 64) * 2;         // whole 64-bit words
     const int64_t b = a.B + 2 * (int64_t)t0;          // number of the tile's bit 0
 
-    for (uint32_t i = threadIdx.x; i < kWheelW1; i += NT) w1[i] = a.wheel1[i];
-    for (uint32_t i = threadIdx.x; i < kWheelW2; i += NT) w2[i] = a.wheel2[i];
+    for (uint32_t i = threadIdx.x; i < kWheelWords; i += NT) wt[i] = a.wheel[i];
     __syncthreads();
 
-    // 1. wheel stamp for 3..19, fix-ups for numbers <= 19 and below 2
+    // 1. stamp of 3..43, fix-ups for numbers <= 43 and below 2
     {
         const int64_t x0 = (b - 1) / 2;               // b = 2 x0 + 1 (exact: b odd)
-        const uint32_t u1 = pmod_u32(x0, kWheelM1);
-        const uint32_t u2 = pmod_u32(x0, kWheelM2);
+        const uint32_t step = 32u * NT;               // pattern advance per loop trip
+        uint32_t a1 = (pmod_u32(x0, kWheelM1) + 32u * threadIdx.x) % kWheelM1;
+        uint32_t a2 = (pmod_u32(x0, kWheelM2) + 32u * threadIdx.x) % kWheelM2;
+        uint32_t a3 = (pmod_u32(x0, kWheelM3) + 32u * threadIdx.x) % kWheelM3;
+        uint32_t a4 = (pmod_u32(x0, kWheelM4) + 32u * threadIdx.x) % kWheelM4;
+        const uint32_t s1 = step % kWheelM1, s2 = step % kWheelM2, s3 = step % kWheelM3, s4 = step % kWheelM4;
         for (uint32_t w = threadIdx.x; w < nw; w += NT) {
-            uint32_t a1 = (u1 + 32u * w) % kWheelM1;
-            uint32_t a2 = (u2 + 32u * w) % kWheelM2;
-            uint32_t v = __funnelshift_r(w1[a1 >> 5], w1[(a1 >> 5) + 1], a1 & 31)
-                       & __funnelshift_r(w2[a2 >> 5], w2[(a2 >> 5) + 1], a2 & 31);
+            uint32_t v = stamp_word(w1, a1) & stamp_word(w2, a2) & stamp_word(w3, a3) & stamp_word(w4, a4);
             const int64_t v0 = b + 64 * (int64_t)w;   // number of this word's bit 0
-            if (v0 <= 19) {
-                // the wheel primes themselves are prime; numbers < 2 are not
+            if (v0 <= 43) {
+                // the stamped primes themselves are prime; numbers < 2 are not
                 for (uint32_t k = 0; k < 32; ++k) {
-                    int64_t num = v0 + 2 * (int64_t)k;
-                    if (num < 2) v &= ~(1u << k);
-                    else if (num == 3 || num == 5 || num == 7 || num == 11 ||
-                             num == 13 || num == 17 || num == 19) v |= 1u << k;
+                    const int64_t num = v0 + 2 * (int64_t)k;
+                    if (num < 2) {
+                        v &= ~(1u << k);
+                    } else if (num <= 43) {
+                        const bool pr = num == 3 || num == 5 || num == 7 || num == 11 || num == 13 ||
+                                        num == 17 || num == 19 || num == 23 || num == 29 || num == 31 ||
+                                        num == 37 || num == 41 || num == 43;
+                        if (pr) v |= 1u << k;
+                    }
                 }
             }
             sm[w] = v;
+            a1 += s1; if (a1 >= kWheelM1) a1 -= kWheelM1;
+            a2 += s2; if (a2 >= kWheelM2) a2 -= kWheelM2;
+            a3 += s3; if (a3 >= kWheelM3) a3 -= kWheelM3;
+            a4 += s4; if (a4 >= kWheelM4) a4 -= kWheelM4;
         }
     }
     __syncthreads();
 
-    // 2. strikes of the primes 23 <= p with p^2 <= the tile's last number
+    // 2. strikes of the primes 47 <= p with p^2 <= the tile's last number
     const int64_t last = b + 2 * (int64_t)(nb - 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long nstrike = 0;
-    for (uint32_t k = warp; k < a.n_warp; k += NT / 32) {
-        const uint32_t p = a.primes[k];
-        const uint64_t pp = (uint64_t)p * p;
-        if ((int64_t)pp > last) break;               // ascending: the rest too
-        uint32_t i0 = first_odd_multiple(b, p, a.recip[k]);
-        if ((int64_t)pp > b) {
-            uint32_t isq = (uint32_t)(((int64_t)pp - b) >> 1);
-            if (isq > i0) i0 = isq;                  // same residue class mod p
+    // 2a. small primes, one warp each: warp w takes the primes w, w + NW, ...;
+    // 32 of them at a time, each lane computing one prime's first index
+    for (uint32_t k0 = warp; k0 < a.n_warp; k0 += 32 * NW) {
+        const uint32_t k = k0 + (uint32_t)lane * NW;
+        uint32_t p = 0, i0 = nb;
+        if (k < a.n_warp) {
+            p = a.primes[k];
+            const uint64_t pp = (uint64_t)p * p;
+            if ((int64_t)pp <= last) {
+                i0 = first_odd_multiple(b, p, a.recip[k]);
+                if ((int64_t)pp > b) {
+                    const uint32_t isq = (uint32_t)(((int64_t)pp - b) >> 1);
+                    if (isq > i0) i0 = isq;              // same residue class mod p
+                }
+            }
         }
-        const uint32_t step = 32u * p;
-        for (uint32_t i = i0 + (uint32_t)lane * p; i < nb; i += step)
-            atomicAnd(&sm[i >> 5], ~(1u << (i & 31)));
-        if (a.strikes && lane == 0 && i0 < nb) nstrike += (nb - 1 - i0) / p + 1;
+        if (a.strikes && i0 < nb) nstrike += (nb - 1 - i0) / p + 1;
+        unsigned pending = __ballot_sync(0xffffffffu, i0 < nb);
+        while (pending) {
+            const int src = __ffs(pending) - 1;
+            pending &= pending - 1;
+            const uint32_t q = __shfl_sync(0xffffffffu, p, src);
+            const uint32_t j0 = __shfl_sync(0xffffffffu, i0, src);
+            const uint32_t step = 32u * q;
+            uint32_t i = j0 + (uint32_t)lane * q;
+#pragma unroll 4
+            for (; i < nb; i += step) atomicAnd(&sm[i >> 5], ~(1u << (i & 31)));
+        }
     }
+    // 2b. larger primes, one thread each
     for (uint32_t k = a.n_warp + threadIdx.x; k < a.n_primes; k += NT) {
         const uint32_t p = a.primes[k];
         const uint64_t pp = (uint64_t)p * p;
@@ -197,7 +225,7 @@ cudaError_t launch_sieve(const SieveArgs& a, int threads, cudaStream_t s)
 {
     if (a.nbits == 0) return cudaSuccess;
     const uint64_t tiles = (a.nbits + a.tile_bits - 1) / a.tile_bits;
-    const size_t smem = (kWheelW1 + kWheelW2 + 3) * 4 + (size_t)a.tile_bits / 8;
+    const size_t smem = (kWheelWords + 3) * 4 + (size_t)a.tile_bits / 8;
     switch (threads) {
     case 128: {
         auto k = k_sieve<128>;
