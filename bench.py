@@ -307,20 +307,26 @@ def main():
     kp = prof[kern]
     launches = max(1, kp["launches"])
     per_launch_ms = kp["ms"] / launches
-    # integer issue peak: 152 SMs x 4 schedulers x 32 lanes x f_max
+    # integer issue peak: 152 SMs x 4 schedulers x 32 lanes x f_max (lane-ops/s)
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12            # T lane-ops/s
     if kern == "cover":
-        ops_per_unit, units = 8.0, work["cover_iterations"]
-        unit_name = "cover word-iterations (8 lane-ops each)"
+        # 4 lane-ops per first-phase (word, prime) step: shift, or, popcount, add;
+        # 4 per second-phase probe: offset load, add, word load, bit test
+        units = work["cover_iterations"]
+        ops = 4.0 * units
+        unit_name = "cover steps (first-phase word steps + second-phase probes), 4 lane-ops each"
     else:
-        ops_per_unit, units = 4.0, work["sieve_strikes"]
-        unit_name = "sieve strikes (4 lane-ops each)"
-    achieved = ops_per_unit * (units / launches) / (per_launch_ms / 1000.0) / 1e12
+        # 4 lane-ops per strike (word index, bit mask, complement, shared atomic AND)
+        # plus 5 per stamped 32-bit word (four pattern reads + store)
+        units = work["sieve_strikes"]
+        ops = 4.0 * units + 5.0 * kp["units"] / 32.0
+        unit_name = "sieve strikes (4 lane-ops) + stamped words (5 lane-ops)"
+    achieved = (ops / launches) / (per_launch_ms / 1000.0) / 1e12
     hbm_bytes = (kp["units"] / launches) / 8.0            # q bits written (sieve) or n read (cover) / 8
     hbm_achieved = hbm_bytes / (per_launch_ms / 1000.0) / 1e9
     roofline = {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
-                "work": unit_name, "work_per_launch": units / launches,
+                "unit": "T lane-ops/s", "frac": achieved / alu_peak, "traffic": None,
+                "work": unit_name, "work_units_per_launch": units / launches,
                 "ms_per_launch": per_launch_ms,
                 "peak_source": "derived: 152 SMs x 128 lanes x %.0f MHz (%s max clock)" % (sm_max, peak_src),
                 "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),

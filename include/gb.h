@@ -159,9 +159,12 @@ int gb_profile_enable(gb_ctx* ctx, int enable);
 int gb_profile_read(gb_ctx* ctx, double* ms, uint64_t* launches, uint64_t* units);
 
 /* Work counted by the kernels while profiling is enabled: bits struck by the
- * segment sieve (every strike of a prime >= 23, duplicates included), and the
- * cover's word iterations, sum over 64-n words of the number of primes applied
- * until the word filled (the bound's count for a word left open). */
+ * segment sieve (every strike of a prime >= 47, duplicates included; primes
+ * 3..43 are stamped from patterns), and the cover's steps: for the two-phase
+ * kernel, first-phase (32-bit word, prime) steps plus second-phase (n, prime)
+ * probes; for the generic kernel, the sum over 64-n words of the number of
+ * primes applied until the word filled (the bound's count for a word left
+ * open). */
 int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterations);
 
 /* Bytes of the odd-only dense bitset for the odd numbers 3..N (Sec. 2.2):

@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
     uint32_t init_pop = 0;
     unsigned long long best = 0;
     int qn = 0;                                             // warp-uniform queue length
+    uint32_t nwords = 0, nprobes = 0;                       // work counts (profiling)
 
     // phase B over the queued n
     auto drain = [&]() {
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
                 }
                 const uint32_t left = a.K - k;
                 if (left < 4) hit &= (1u << left) - 1u;
+                nprobes += hit ? (uint32_t)__ffs(hit) : (left < 4 ? left : 4u);
                 if (hit) {
                     const uint32_t kk = k + (__ffs(hit) - 1);
                     atomicAdd(&shist[kk + 1], 1u);
@@ -217,6 +219,7 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
             for (int t = 0; t < NR; ++t) R[t] = 0;
         }
         init_pop += __popc(C);
+        nwords += active;
         phase_a<NR, KH>(std::make_integer_sequence<int, KA>{}, R, C, cum);
 
         // queue the n still open
@@ -243,6 +246,13 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
     }
     if (qn) drain();
 
+    if (a.iters) {
+        // first-phase word steps plus second-phase probes
+        const unsigned long long wk = (unsigned long long)nwords * KA + nprobes;
+        unsigned long long t = wk;
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0 && t) atomicAdd(a.iters, t);
+    }
     // first-phase histogram from the cumulative counts
     uint32_t prev = __reduce_add_sync(0xffffffffu, init_pop);
 #pragma unroll
