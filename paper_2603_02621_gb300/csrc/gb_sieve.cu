@@ -89,6 +89,14 @@ __device__ __forceinline__ uint32_t pmod_u32(int64_t x, uint32_t M)
     return (uint32_t)(r < 0 ? r + M : r);
 }
 
+// clear bit i of the tile: word i/32 at byte offset (i >> 3) & ~3, mask
+// ~(1 << (i & 31)) as a rotate of 0xfffffffe (the funnel shift takes i mod 32)
+__device__ __forceinline__ void strike(uint32_t* sm, uint32_t i)
+{
+    atomicAnd(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sm) + ((i >> 3) & ~3u)),
+              __funnelshift_l(0xfffffffeu, 0xfffffffeu, i));
+}
+
 // one stamp table read at pattern offset a (a < period): 32 bits from bit a
 __device__ __forceinline__ uint32_t stamp_word(const uint32_t* tab, uint32_t a)
 {
@@ -180,8 +188,14 @@ __global__ void __launch_bounds__(NT) k_sieve(const SieveArgs a)
             const uint32_t j0 = __shfl_sync(0xffffffffu, i0, src);
             const uint32_t step = 32u * q;
             uint32_t i = j0 + (uint32_t)lane * q;
-#pragma unroll 4
-            for (; i < nb; i += step) atomicAnd(&sm[i >> 5], ~(1u << (i & 31)));
+            // step <= 2^15 and i < 2^20: no wrap below
+            for (; i + 3 * step < nb; i += 4 * step) {
+                strike(sm, i);
+                strike(sm, i + step);
+                strike(sm, i + 2 * step);
+                strike(sm, i + 3 * step);
+            }
+            for (; i < nb; i += step) strike(sm, i);
         }
     }
     // 2b. larger primes, one thread each
@@ -196,7 +210,13 @@ __global__ void __launch_bounds__(NT) k_sieve(const SieveArgs a)
         }
         if (a.strikes && i < nb) nstrike += (nb - 1 - i) / p + 1;
         // i < 2^20 and p < 3.1e9 (p^2 < 2^63): i + p cannot wrap
-        for (; i < nb; i += p) atomicAnd(&sm[i >> 5], ~(1u << (i & 31)));
+        if (p < (1u << 20)) {
+            for (; i + p < nb; i += 2 * p) {
+                strike(sm, i);
+                strike(sm, i + p);
+            }
+        }
+        for (; i < nb; i += p) strike(sm, i);
     }
     if (a.strikes) {
         for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);
