@@ -151,11 +151,10 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P,
 
 /* Per-kernel device time, measured with CUDA events recorded on the
  * context's stream around every launch while profiling is enabled.  Kinds:
- * 0 segment sieve (units: q bits sieved), 1 cover, first phase or generic
- * kernel (units: even n), 2 retry pass (units: even n of the slabs it ran
- * on), 3 reductions and the max-only pass (units: segments), 4 cover second
- * phase (units: even n).  gb_profile_enable resets the counters. */
-#define GB_PROF_KINDS 5
+ * 0 segment sieve (units: q bits sieved), 1 cover (units: even n), 2 retry
+ * pass (units: even n of the slabs it ran on), 3 reductions and the max-only
+ * pass (units: segments).  gb_profile_enable resets the counters. */
+#define GB_PROF_KINDS 4
 int gb_profile_enable(gb_ctx* ctx, int enable);
 int gb_profile_read(gb_ctx* ctx, double* ms, uint64_t* launches, uint64_t* units);
 

@@ -23,7 +23,7 @@
 
 namespace {
 
-enum { kProfSieve = 0, kProfCover = 1, kProfRetry = 2, kProfReduce = 3, kProfProbe = 4 };
+enum { kProfSieve = 0, kProfCover = 1, kProfRetry = 2, kProfReduce = 3 };
 
 thread_local std::string g_last_error;
 
@@ -103,7 +103,6 @@ struct gb_ctx {
     DevBuf q;                         // slab q window
     DevBuf hist, maxkey, maxkey2, unres, retry, retry_count, summary, rows, merged, pmin, counter, totals, records;
     DevBuf work;                      // profiling work counters: [0] sieve strikes, [1] cover iterations
-    DevBuf open;                      // open-n list of the two-phase cover
     uint64_t work_strikes = 0, work_iters = 0;
     int warp_split = 0;               // sieving primes below this strike one warp each
     bool generic_cover = false;       // force the generic cover kernel (GB_COVER=generic)
@@ -373,7 +372,7 @@ void gb_destroy(gb_ctx* ctx)
     else cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->primes, &ctx->recip, &ctx->wheel, &ctx->q, &ctx->hist,
                       &ctx->maxkey, &ctx->maxkey2, &ctx->unres, &ctx->retry, &ctx->retry_count, &ctx->summary,
-                      &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work, &ctx->open};
+                      &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work};
     for (DevBuf* b : bufs) b->release();
     delete ctx;
 }
@@ -484,21 +483,16 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
     const uint64_t slab_segs = std::min<uint64_t>(spb, nseg);
     const uint64_t q_words = slab_words + H / 128 + 2;
     const uint32_t retry_cap = (uint32_t)std::min<uint64_t>(slab_words, 1u << 21);
-    // open-n list of the two-phase cover: 1/16 of the slab's n (far above the
-    // few per thousand met in practice); an overflow redoes the call generically
-    const uint32_t open_cap = (uint32_t)std::max<uint64_t>(1 << 16, std::min<uint64_t>(slab_n / 16, 0xffffffffull));
     if ((rc = ctx->q.ensure(q_words * 8)) ||
         (rc = ctx->hist.ensure(slab_segs * hist_stride * 4)) ||
         (rc = ctx->maxkey.ensure(slab_segs * 8)) || (rc = ctx->maxkey2.ensure(slab_segs * 8)) ||
         (rc = ctx->unres.ensure(slab_segs * 8)) ||
         (retry && (rc = ctx->retry.ensure((size_t)retry_cap * sizeof(gb::RetryItem)))) ||
         (rc = ctx->retry_count.ensure(16)) ||
-        (rc = ctx->open.ensure((size_t)open_cap * 4)) ||
         (out->pmin && !pmin_dev && (rc = ctx->pmin.ensure(slab_n * 4))))
         return rc;
 
     unsigned int overflow_total = 0;
-    bool open_overflow = false;
     for (uint64_t s0 = 0; s0 < nseg; s0 += spb) {
         const uint64_t ns = std::min<uint64_t>(spb, nseg - s0);
         const uint64_t A0 = lo + 2 * s0 * S;
@@ -511,7 +505,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         GB_CUDA(cudaMemsetAsync(ctx->maxkey.p, 0, ns * 8, s));
         GB_CUDA(cudaMemsetAsync(ctx->maxkey2.p, 0, ns * 8, s));
         GB_CUDA(cudaMemsetAsync(ctx->unres.p, 0, ns * 8, s));
-        GB_CUDA(cudaMemsetAsync(ctx->retry_count.p, 0, 16, s));   // [0] retry items, [1] open n
+        GB_CUDA(cudaMemsetAsync(ctx->retry_count.p, 0, 16, s));
         uint32_t* pm = nullptr;
         if (out->pmin) {
             pm = pmin_dev ? out->pmin + (s0 * S) : ctx->pmin.as<uint32_t>();
@@ -546,16 +540,10 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         // two-phase kernel unless a p_min array is wanted (the generic kernel
         // writes it) or the pass has too few primes for its first phase
         const int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
-        gb::OpenList ol{ctx->open.as<uint32_t>(), ctx->retry_count.as<unsigned int>() + 1, open_cap};
         ctx->prof_begin(kProfCover, n_count);
-        if (KA) GB_CUDA(gb::launch_cover_fast(ca, ol, KA, s));
+        if (KA) GB_CUDA(gb::launch_cover_fast(ca, KA, s));
         else GB_CUDA(gb::launch_cover(ca, (int)cfg.cta_threads, s));
         ctx->prof_end();
-        if (KA) {
-            ctx->prof_begin(kProfProbe, n_count);
-            GB_CUDA(gb::launch_cover_probe(ca, ol, KA, s));
-            ctx->prof_end();
-        }
 
         if (retry) {
             gb::RetryArgs ra{};
@@ -609,24 +597,14 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         GB_CUDA(gb::launch_reduce(rd, s));
         ctx->prof_end();
 
-        if (retry || KA) {
-            unsigned int cnt[2] = {0, 0};
-            GB_CUDA(cudaMemcpyAsync(cnt, ctx->retry_count.p, 8, cudaMemcpyDeviceToHost, s));
+        if (retry) {
+            unsigned int cnt = 0;
+            GB_CUDA(cudaMemcpyAsync(&cnt, ctx->retry_count.p, 4, cudaMemcpyDeviceToHost, s));
             GB_CUDA(cudaStreamSynchronize(s));
-            if (cnt[0] > retry_cap) overflow_total += cnt[0] - retry_cap;
-            if (cnt[1] > open_cap) open_overflow = true;
+            if (cnt > retry_cap) overflow_total += cnt - retry_cap;
         }
         if (out->pmin && !pmin_dev)
             GB_CUDA(cudaMemcpyAsync(out->pmin + s0 * S, pm, n_count * 4, cudaMemcpyDeviceToHost, s));
-    }
-    if (open_overflow) {
-        // more n stayed open after the first phase than the list holds: redo
-        // the call with the generic cover kernel
-        const bool saved = ctx->generic_cover;
-        ctx->generic_cover = true;
-        rc = gb_verify_range(ctx, lo, hi, P, out);
-        ctx->generic_cover = saved;
-        return rc;
     }
     if (overflow_total) {
         // the retry list could not hold every word left open: redo in one pass to Pf

@@ -15,13 +15,16 @@
 // registers.  A step is then
 //     s = funnel-shift of two window registers,  C |= s,  cum_k += popc(C)
 // and the histogram of the first phase follows from the cumulative counts:
-// #{n : p_min(n) = p_k} = cum_k - cum_{k-1}.  The n still open after KA primes
-// (a few per thousand near 1e10) are appended to a slab-wide list.
+// #{n : p_min(n) = p_k} = cum_k - cum_{k-1}.
 //
-// Phase B (k_cover_probe).  Each listed n probes the bit of Q at j + d_k for
-// k = KA, KA+1, ... (four probes per step); the first set bit gives p_min.  One
-// slab-wide list keeps every thread of the GPU busy; an n still open after K
-// primes goes to the retry pass (or counts as unresolved).
+// Phase B, in the same kernel while the CTA's part of Q is still in L1.  The n
+// still open after KA primes (a few per thousand near 1e10) are queued per warp
+// in shared memory; each probes the bit of Q at j + d_k for k = KA, KA+1, ...
+// (four probes per step), the first set bit giving p_min.  A lane keeps the n
+// it is working on in registers across drains and takes a new one from the
+// queue when it finishes, and a drain stops once the queue is handed out, so
+// only the last drain of a CTA waits for its slowest n.  An n still open after
+// K primes goes to the retry pass (or counts as unresolved).
 //
 // The largest p_min of a segment, with its smallest n, comes from phase B (or
 // the retry pass).  A segment where no n needed more than KA primes gets its
@@ -77,15 +80,31 @@ __device__ __forceinline__ void phase_a(std::integer_sequence<int, K...>, const 
     (phase_a_step<K, NR, KH>(R, C, cum), ...);
 }
 
+constexpr int kQueueCap = 1024;      // queued n per warp (one round adds at most 1024)
+constexpr int kQueueRun = 160;       // drain once this many n wait
+
+// shared-memory layout (uint32 units): offsets table with 4 zero entries past
+// K (the 4-wide probes may read them; their results are masked), histogram,
+// then the 16-bit per-warp queues
+__host__ __device__ constexpr uint32_t sd_len(uint32_t K) { return (K + 4 + 3) & ~3u; }
+__host__ __device__ constexpr uint32_t hist_len(uint32_t K) { return (K + 1 + 3) & ~3u; }
+
 template <int NT, int KA>
-__global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a, const OpenList open)
+__global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
 {
     constexpr int NW = NT / 32;
     constexpr int NR = window_regs(KA);
     constexpr int KH = KA / 2;
-    __shared__ uint32_t shist[KA + 1];
+    extern __shared__ uint32_t smem[];
+    uint32_t* sd = smem;                                    // d_k, K entries + 4 pad (0)
+    uint32_t* shist = sd + sd_len(a.K);                     // K + 1 counters
+    uint16_t* queues = reinterpret_cast<uint16_t*>(shist + hist_len(a.K));   // NW * kQueueCap
+    __shared__ unsigned long long smax;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // queue entry: round << 10 | lane << 5 | bit, i.e. the n at CTA-relative
+    // index 32 * (32 * (NW * round + warp) + lane) + bit
+    uint16_t* queue = queues + warp * kQueueCap;
 
     // this CTA's words (32-bit words of C, 32 even n each)
     const uint64_t wps = 2ull * a.words_per_seg;
@@ -98,7 +117,9 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a, const Open
     if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
     if (w_end > n_words32) w_end = n_words32;
 
-    for (int k = threadIdx.x; k <= KA; k += NT) shist[k] = 0;
+    for (uint32_t k = threadIdx.x; k < sd_len(a.K); k += NT) sd[k] = k < a.K ? (a.H - a.primes[1 + k] - 1) >> 1 : 0u;
+    for (uint32_t k = threadIdx.x; k <= a.K; k += NT) shist[k] = 0;
+    if (threadIdx.x == 0) smax = 0;
     __syncthreads();
 
     const uint32_t* Qc = reinterpret_cast<const uint32_t*>(a.Q) + w_begin;   // CTA-relative words
@@ -106,14 +127,81 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a, const Open
     const uint32_t nw_cta = (uint32_t)(w_end > w_begin ? w_end - w_begin : 0);
     const uint64_t n_left = a.n_count - 32 * w_begin;       // n from the CTA's first n to the slab end
     const uint32_t n_rel_end = (uint32_t)(n_left < 32ull * nw_cta ? n_left : 32ull * nw_cta);
-    const uint32_t slab_n0 = (uint32_t)(32 * w_begin);      // slab-relative n of the CTA's first n
+    const uint32_t j_cta = (uint32_t)(32 * (w_begin - seg_w0));   // segment-relative n of the CTA's first n
 
     uint32_t cum[KH];
 #pragma unroll
     for (int k = 0; k < KH; ++k) cum[k] = 0;
-    uint32_t init_pop = 0, nwords = 0;
+    uint32_t init_pop = 0, nwords = 0, nprobes = 0;
+    unsigned long long best = 0;
+    int qn = 0;                                             // warp-uniform queue length
 
-    for (uint32_t wbase = 32 * warp; wbase < nw_cta; wbase += 32 * NW) {
+    // phase-B state of this lane, kept across drains
+    bool act = false;
+    uint32_t rel = 0, k = KA;
+
+    auto decode = [&](uint32_t q) {
+        return ((((q >> 10) * NW + (uint32_t)warp) * 32 + ((q >> 5) & 31)) << 5) | (q & 31);
+    };
+    // hand out the queued n; with final set, also finish every n in flight
+    auto drain = [&](bool final) {
+        __syncwarp();
+        uint32_t next = 0;
+        for (;;) {
+            const unsigned idle = __ballot_sync(0xffffffffu, !act);
+            if (idle && next < (uint32_t)qn) {
+                const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
+                if (!act && next + rank < (uint32_t)qn) {
+                    act = true;
+                    rel = decode(queue[next + rank]);
+                    k = KA;
+                }
+                next += __popc(idle);
+            }
+            if (!final && next >= (uint32_t)qn) break;      // queue handed out
+            if (!__any_sync(0xffffffffu, act)) break;
+            if (act) {
+                uint32_t hit = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t i = rel + sd[k + t];
+                    hit |= ((__ldg(Qc + (i >> 5)) >> (i & 31)) & 1u) << t;
+                }
+                const uint32_t left = a.K - k;
+                if (left < 4) hit &= (1u << left) - 1u;
+                nprobes += hit ? (uint32_t)__ffs(hit) : (left < 4 ? left : 4u);
+                if (hit) {
+                    const uint32_t kk = k + (__ffs(hit) - 1);
+                    atomicAdd(&shist[kk + 1], 1u);
+                    const unsigned long long key =
+                        ((unsigned long long)(kk + 2) << 32) | (0xffffffffull - (j_cta + rel));
+                    if (key > best) best = key;
+                    act = false;
+                } else if (left <= 4) {
+                    // open after every prime of this pass
+                    const uint64_t jn = 32 * w_begin + rel;            // slab-relative n index
+                    bool queued = false;
+                    if (a.retry) {
+                        const unsigned int slot = atomicAdd(a.retry_count, 1u);
+                        if (slot < a.retry_cap) {
+                            a.retry[slot].w = jn >> 6;
+                            a.retry[slot].C = ~(1ull << (jn & 63));
+                            queued = true;
+                        }
+                    }
+                    if (!queued) atomicAdd(&a.unresolved[seg], 1ull);
+                    act = false;
+                } else {
+                    k += 4;
+                }
+            }
+        }
+        __syncwarp();
+        qn = 0;
+    };
+
+    uint32_t round = 0;
+    for (uint32_t wbase = 32 * warp; wbase < nw_cta; wbase += 32 * NW, ++round) {
         const uint32_t wrel = wbase + lane;
         const bool active = wrel < nw_cta;
         uint32_t C = 0xffffffffu;
@@ -124,7 +212,7 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a, const Open
             if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);   // past the slab end
             if (a.has_n4 && w_begin + wrel == 0) {
                 C |= 1u;                                     // n = 4 = 2 + 2
-                atomicAdd(&a.hist[(uint64_t)seg * a.hist_stride], 1u);
+                atomicAdd(&shist[0], 1u);
             }
 #pragma unroll
             for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - t);
@@ -136,106 +224,56 @@ __global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a, const Open
         nwords += active;
         phase_a<NR, KH>(std::make_integer_sequence<int, KA>{}, R, C, cum);
 
-        // append the n still open
+        // queue the n still open
         uint32_t m = ~C;
         if (!__any_sync(0xffffffffu, m != 0)) continue;
         const uint32_t cnt = __popc(m);
-        uint32_t pre = cnt;                                  // inclusive prefix over lanes
+        uint32_t incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, pre, o);
-            if (lane >= o) pre += v;
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        uint32_t base = 0;
-        if (lane == 31) base = atomicAdd(open.count, pre);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        uint32_t pos = base + pre - cnt;
-        const uint32_t j0 = slab_n0 + 32 * wrel;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (qn + (int)total > kQueueCap) drain(false);
+        uint32_t pos = qn + incl - cnt;
+        const uint32_t tag = (round << 10) | ((uint32_t)lane << 5);
         while (m) {
             const uint32_t b = __ffs(m) - 1;
             m &= m - 1;
-            if (pos < open.cap) open.n[pos] = j0 + b;
-            ++pos;
+            queue[pos++] = (uint16_t)(tag | b);
         }
+        qn += (int)total;
+        if (qn >= kQueueRun) drain(false);
     }
+    drain(true);
 
     if (a.iters) {
-        // first-phase word steps
-        unsigned long long t = (unsigned long long)nwords * KA;
+        // first-phase word steps plus second-phase probes
+        unsigned long long t = (unsigned long long)nwords * KA + nprobes;
         for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0 && t) atomicAdd(a.iters, t);
     }
     // first-phase histogram from the cumulative counts
     uint32_t prev = __reduce_add_sync(0xffffffffu, init_pop);
 #pragma unroll
-    for (int k = 0; k < KA; ++k) {
-        const uint32_t v = (k & 1) ? cum[k >> 1] >> 16 : cum[k >> 1] & 0xffffu;
+    for (int kk = 0; kk < KA; ++kk) {
+        const uint32_t v = (kk & 1) ? cum[kk >> 1] >> 16 : cum[kk >> 1] & 0xffffu;
         const uint32_t tot = __reduce_add_sync(0xffffffffu, v);
-        if (lane == 0 && tot != prev) atomicAdd(&shist[k + 1], tot - prev);
+        if (lane == 0 && tot != prev) atomicAdd(&shist[kk + 1], tot - prev);
         prev = tot;
     }
+    // second-phase maximum: warp, CTA, segment
+    const uint32_t khi = (uint32_t)(best >> 32);
+    const uint32_t mhi = __reduce_max_sync(0xffffffffu, khi);
+    const uint32_t klo = khi == mhi ? (uint32_t)best : 0u;
+    const uint32_t mlo = __reduce_max_sync(0xffffffffu, klo);
+    if (lane == 0 && mhi) atomicMax(&smax, ((unsigned long long)mhi << 32) | mlo);
     __syncthreads();
     uint32_t* hrow = a.hist + (uint64_t)seg * a.hist_stride;
-    for (int k = 1 + threadIdx.x; k <= KA; k += NT)
-        if (shist[k]) atomicAdd(&hrow[k], shist[k]);
-}
-
-// phase B: every thread walks the open list with a grid stride; one flat loop
-// (probe up to four primes, or move to the next listed n) keeps lanes in step
-__global__ void __launch_bounds__(256) k_cover_probe(const CoverArgs a, const OpenList open, uint32_t KA)
-{
-    const uint32_t total = min(*open.count, open.cap);
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const uint32_t* Q32 = reinterpret_cast<const uint32_t*>(a.Q);
-    const uint32_t spn = 64 * a.words_per_seg;              // n per segment
-    uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t j = 0, k = KA, nprobes = 0;
-    if (e < total) j = open.n[e];
-    while (e < total) {
-        // probe k .. k+3; primes past K are never read
-        uint32_t hit = 0;
-        const uint32_t left = a.K - k;
-        const uint32_t np = left < 4 ? left : 4u;
-        for (uint32_t t = 0; t < np; ++t) {
-            const uint32_t p = a.primes[1 + k + t];
-            const uint64_t i = (uint64_t)j + ((a.H - p - 1) >> 1);
-            hit |= ((__ldg(Q32 + (i >> 5)) >> (i & 31)) & 1u) << t;
-        }
-        nprobes += hit ? (uint32_t)__ffs(hit) : np;
-        if (hit || left <= 4) {
-            const uint32_t seg = j / spn;
-            if (hit) {
-                const uint32_t kk = k + (__ffs(hit) - 1);
-                atomicAdd(&a.hist[(uint64_t)seg * a.hist_stride + kk + 1], 1u);
-                const unsigned long long key =
-                    ((unsigned long long)(kk + 2) << 32) | (0xffffffffull - (j - seg * spn));
-                // keys only grow: a stale read can only cost an extra atomic
-                if (key > *(volatile unsigned long long*)&a.maxkey[seg]) atomicMax(&a.maxkey[seg], key);
-            } else {
-                // open after every prime of this pass
-                bool queued = false;
-                if (a.retry) {
-                    const unsigned int slot = atomicAdd(a.retry_count, 1u);
-                    if (slot < a.retry_cap) {
-                        a.retry[slot].w = j >> 6;
-                        a.retry[slot].C = ~(1ull << (j & 63));
-                        queued = true;
-                    }
-                }
-                if (!queued) atomicAdd(&a.unresolved[seg], 1ull);
-            }
-            e += stride;
-            k = KA;
-            if (e < total) j = open.n[e];
-        } else {
-            k += 4;
-        }
-    }
-    if (a.iters) {
-        unsigned long long t = nprobes;
-        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if ((threadIdx.x & 31) == 0 && t) atomicAdd(a.iters, t);
-    }
+    for (uint32_t kk = threadIdx.x; kk <= a.K; kk += NT)
+        if (shist[kk]) atomicAdd(&hrow[kk], shist[kk]);
+    if (threadIdx.x == 0 && smax) atomicMax(&a.maxkey[seg], smax);
 }
 
 int cover_fast_phase_primes(uint32_t K, uint64_t n_hi)
@@ -252,33 +290,31 @@ int cover_fast_phase_primes(uint32_t K, uint64_t n_hi)
 }
 
 template <int KA>
-static cudaError_t launch_ka(const CoverArgs& a, const OpenList& open, cudaStream_t s)
+static cudaError_t launch_ka(const CoverArgs& a, cudaStream_t s)
 {
     constexpr int NT = 256;
     const unsigned grid = a.nseg * a.chunks_per_seg;
     if (grid == 0) return cudaSuccess;
-    k_cover_fast<NT, KA><<<grid, NT, 0, s>>>(a, open);
+    const size_t smem = (size_t)(sd_len(a.K) + hist_len(a.K)) * 4 + (size_t)(NT / 32) * kQueueCap * 2;
+    auto k = k_cover_fast<NT, KA>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cover_fast(const CoverArgs& a, const OpenList& open, int KA, cudaStream_t s)
+cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s)
 {
-    // 16-bit counters: a lane sums at most 32 per word over its words of a CTA
-    if (2ull * a.cta_words > 2047ull * 256) return cudaErrorInvalidValue;
+    // 16-bit queue entries hold rounds < 64 and 16-bit counters a lane's sum of
+    // at most 32 per word: at most 64 words per lane per CTA
+    if (2ull * a.cta_words > 64ull * 256) return cudaErrorInvalidValue;
     switch (KA) {
-    case 32: return launch_ka<32>(a, open, s);
-    case 48: return launch_ka<48>(a, open, s);
-    case 64: return launch_ka<64>(a, open, s);
-    case 96: return launch_ka<96>(a, open, s);
-    case 128: return launch_ka<128>(a, open, s);
+    case 32: return launch_ka<32>(a, s);
+    case 48: return launch_ka<48>(a, s);
+    case 64: return launch_ka<64>(a, s);
+    case 96: return launch_ka<96>(a, s);
+    case 128: return launch_ka<128>(a, s);
     default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_cover_probe(const CoverArgs& a, const OpenList& open, int KA, cudaStream_t s)
-{
-    k_cover_probe<<<152 * 8, 256, 0, s>>>(a, open, (uint32_t)KA);
-    return cudaGetLastError();
 }
 
 }  // namespace gb

@@ -125,20 +125,14 @@ struct CoverArgs {
 };
 cudaError_t launch_cover(const CoverArgs& a, int threads, cudaStream_t s);
 
-// Two-phase cover.  Phase A (k_cover_fast): the first KA odd primes on every
-// 32-bit coverage word, unrolled; the n still open are appended to a list.
-// Phase B (k_cover_probe): each listed n probes the primes KA+1 .. K in order.
-// Needs K >= KA, H = 4 (mod 64) and no p_min array; does not record the
-// maximum of words closed in phase A (the generic kernel in max-only mode
-// fills it in for segments where nothing else set a key).
-struct OpenList {
-    uint32_t* n;                // slab-relative n index of each open n
-    unsigned int* count;        // entries appended (may exceed cap: overflow)
-    uint32_t cap;
-};
+// Two-phase cover (k_cover_fast): the first KA odd primes on every 32-bit
+// coverage word, unrolled; then, in the same kernel, each n still open probes
+// the primes KA+1 .. K in order.  Needs K >= KA, H = 4 (mod 64) and no p_min
+// array; does not record the maximum of words closed in the first phase (the
+// generic kernel in max-only mode fills it in for segments where nothing else
+// set a key).
 int cover_fast_phase_primes(uint32_t K, uint64_t n_hi);   // KA for K primes near n_hi (0: none)
-cudaError_t launch_cover_fast(const CoverArgs& a, const OpenList& open, int KA, cudaStream_t s);
-cudaError_t launch_cover_probe(const CoverArgs& a, const OpenList& open, int KA, cudaStream_t s);
+cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s);
 
 struct RetryArgs {
     const uint64_t* Q;

@@ -197,8 +197,8 @@ def gb_verify_range(ctx: int, lo: int, hi: int, P: int = 0, *, hist_cap: int = 0
     return out
 
 
-GB_PROF_KINDS = 5
-PROF_NAMES = ("sieve", "cover", "retry", "reduce", "probe")
+GB_PROF_KINDS = 4
+PROF_NAMES = ("sieve", "cover", "retry", "reduce")
 
 
 def gb_profile_enable(ctx: int, enable: bool = True) -> None:
