@@ -106,6 +106,7 @@ struct gb_ctx {
     uint64_t work_strikes = 0, work_iters = 0;
     int warp_split = 0;               // sieving primes below this strike one warp each
     bool generic_cover = false;       // force the generic cover kernel (GB_COVER=generic)
+    int ka_override = 0;              // first-phase length of the two-phase cover (GB_KA)
 
     // per-kernel device time (CUDA events on the context's stream around each launch)
     bool profiling = false;
@@ -355,6 +356,10 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     ctx->warp_split = (int)std::min<uint32_t>(1024, c.tile_bits / 64);
     if (const char* e = getenv("GB_WARP_SPLIT")) ctx->warp_split = atoi(e);
     if (const char* e = getenv("GB_COVER")) ctx->generic_cover = std::string(e) == "generic";
+    if (const char* e = getenv("GB_KA")) {
+        const int v = atoi(e);
+        if (v == 32 || v == 48 || v == 64 || v == 96 || v == 128) ctx->ka_override = v;
+    }
     rc = build_primes(ctx);
     if (rc) {
         gb_destroy(ctx);
@@ -453,9 +458,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
     const uint64_t last_num = hi + 2 * 1024 + H;          // generous bound of the sieve window
     if (isqrt_u64(last_num) > ctx->L) return fail(GB_EINVAL, "hi beyond base_limit^2");
     const uint32_t hist_stride = Kf + 1;
-    // segments per slab: at most slab_bits q-bits, and fewer than 2^32 n (the
-    // two-phase cover lists open n by 32-bit slab-relative index)
-    const uint64_t spb = std::max<uint64_t>(1, std::min<uint64_t>(cfg.slab_bits, 0xffffffffull) / S);
+    const uint64_t spb = std::max<uint64_t>(1, cfg.slab_bits / S);   // segments per slab
     GB_CUDA(cudaSetDevice(cfg.device));
     cudaStream_t s = ctx->stream;
 
@@ -539,7 +542,8 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         ca.iters = ctx->work_ptr(1);
         // two-phase kernel unless a p_min array is wanted (the generic kernel
         // writes it) or the pass has too few primes for its first phase
-        const int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
+        int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
+        if (KA && ctx->ka_override && (uint32_t)ctx->ka_override <= K1) KA = ctx->ka_override;
         ctx->prof_begin(kProfCover, n_count);
         if (KA) GB_CUDA(gb::launch_cover_fast(ca, KA, s));
         else GB_CUDA(gb::launch_cover(ca, (int)cfg.cta_threads, s));

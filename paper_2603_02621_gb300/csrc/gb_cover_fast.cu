@@ -89,8 +89,9 @@ constexpr int kQueueRun = 160;       // drain once this many n wait
 __host__ __device__ constexpr uint32_t sd_len(uint32_t K) { return (K + 4 + 3) & ~3u; }
 __host__ __device__ constexpr uint32_t hist_len(uint32_t K) { return (K + 1 + 3) & ~3u; }
 
+// CTAs of 256 threads per SM: four up to KA = 64 (64 registers), three at 96
 template <int NT, int KA>
-__global__ void __launch_bounds__(NT) k_cover_fast(const CoverArgs a)
+__global__ void __launch_bounds__(NT, KA <= 64 ? 4 : KA <= 96 ? 3 : 2) k_cover_fast(const CoverArgs a)
 {
     constexpr int NW = NT / 32;
     constexpr int NR = window_regs(KA);
