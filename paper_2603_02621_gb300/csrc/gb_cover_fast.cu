@@ -56,8 +56,13 @@ __host__ __device__ constexpr int window_regs(int KA)
     return (int)(((odd_prime(KA - 1) - 3) / 2 + 31) / 32) + 1;
 }
 
-// cumulative counts are kept two per register (16-bit halves): a lane adds at
-// most 32 per word and handles fewer than 2^11 words per CTA
+// cumulative counts are kept three per register (10-bit fields): a lane adds
+// at most 32 per word and handles at most 31 words per CTA (32 * 31 < 2^10)
+constexpr int kCumBits = 10;
+constexpr uint32_t kCumMask = (1u << kCumBits) - 1;
+constexpr int kMaxWordsPerLane = 31;
+__host__ __device__ constexpr int cum_regs(int KA) { return (KA + 2) / 3; }
+
 template <int K, int NR, int KH>
 __device__ __forceinline__ void phase_a_step(const uint32_t (&R)[NR], uint32_t& C, uint32_t (&cum)[KH])
 {
@@ -69,8 +74,8 @@ __device__ __forceinline__ void phase_a_step(const uint32_t (&R)[NR], uint32_t& 
     if constexpr (sh == 0) s = R[c];
     else s = __funnelshift_r(R[c], R[c - 1], sh);
     C |= s;
-    if constexpr (K & 1) cum[K >> 1] += __popc(C) << 16;
-    else cum[K >> 1] += __popc(C);
+    if constexpr (K % 3 == 0) cum[K / 3] += __popc(C);
+    else cum[K / 3] += __popc(C) << (kCumBits * (K % 3));
 }
 
 template <int NR, int KH, int... K>
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(NT, KA <= 64 ? 4 : KA <= 96 ? 3 : 2) k_cover_f
 {
     constexpr int NW = NT / 32;
     constexpr int NR = window_regs(KA);
-    constexpr int KH = KA / 2;
+    constexpr int KH = cum_regs(KA);
     extern __shared__ uint32_t smem[];
     uint32_t* sd = smem;                                    // d_k, K entries + 4 pad (0)
     uint32_t* shist = sd + sd_len(a.K);                     // K + 1 counters
@@ -133,13 +138,18 @@ __global__ void __launch_bounds__(NT, KA <= 64 ? 4 : KA <= 96 ? 3 : 2) k_cover_f
     uint32_t cum[KH];
 #pragma unroll
     for (int k = 0; k < KH; ++k) cum[k] = 0;
-    uint32_t init_pop = 0, nwords = 0, nprobes = 0;
-    unsigned long long best = 0;
+    uint32_t init_pop = 0, nwords = 0;
     int qn = 0;                                             // warp-uniform queue length
 
-    // phase-B state of this lane, kept across drains
-    bool act = false;
-    uint32_t rel = 0, k = KA;
+    // phase-B state of each lane, parked in shared memory between drains so
+    // that it takes no registers during the first phase (k = 0: no n held)
+    __shared__ uint32_t hold_rel[NT];
+    __shared__ uint32_t hold_k[NT];
+    __shared__ uint32_t hold_probes[NT];
+    __shared__ unsigned long long hold_best[NT];
+    hold_k[threadIdx.x] = 0;
+    hold_probes[threadIdx.x] = 0;
+    hold_best[threadIdx.x] = 0;
 
     auto decode = [&](uint32_t q) {
         return ((((q >> 10) * NW + (uint32_t)warp) * 32 + ((q >> 5) & 31)) << 5) | (q & 31);
@@ -147,6 +157,11 @@ __global__ void __launch_bounds__(NT, KA <= 64 ? 4 : KA <= 96 ? 3 : 2) k_cover_f
     // hand out the queued n; with final set, also finish every n in flight
     auto drain = [&](bool final) {
         __syncwarp();
+        uint32_t k = hold_k[threadIdx.x];
+        bool act = k != 0;
+        uint32_t rel = hold_rel[threadIdx.x];
+        uint32_t nprobes = hold_probes[threadIdx.x];
+        unsigned long long best = hold_best[threadIdx.x];
         uint32_t next = 0;
         for (;;) {
             const unsigned idle = __ballot_sync(0xffffffffu, !act);
@@ -197,6 +212,10 @@ __global__ void __launch_bounds__(NT, KA <= 64 ? 4 : KA <= 96 ? 3 : 2) k_cover_f
                 }
             }
         }
+        hold_k[threadIdx.x] = act ? k : 0u;
+        hold_rel[threadIdx.x] = rel;
+        hold_probes[threadIdx.x] = nprobes;
+        hold_best[threadIdx.x] = best;
         __syncwarp();
         qn = 0;
     };
@@ -249,9 +268,10 @@ __global__ void __launch_bounds__(NT, KA <= 64 ? 4 : KA <= 96 ? 3 : 2) k_cover_f
     }
     drain(true);
 
+    const unsigned long long best = hold_best[threadIdx.x];
     if (a.iters) {
         // first-phase word steps plus second-phase probes
-        unsigned long long t = (unsigned long long)nwords * KA + nprobes;
+        unsigned long long t = (unsigned long long)nwords * KA + hold_probes[threadIdx.x];
         for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0 && t) atomicAdd(a.iters, t);
     }
@@ -259,7 +279,7 @@ __global__ void __launch_bounds__(NT, KA <= 64 ? 4 : KA <= 96 ? 3 : 2) k_cover_f
     uint32_t prev = __reduce_add_sync(0xffffffffu, init_pop);
 #pragma unroll
     for (int kk = 0; kk < KA; ++kk) {
-        const uint32_t v = (kk & 1) ? cum[kk >> 1] >> 16 : cum[kk >> 1] & 0xffffu;
+        const uint32_t v = (cum[kk / 3] >> (kCumBits * (kk % 3))) & kCumMask;
         const uint32_t tot = __reduce_add_sync(0xffffffffu, v);
         if (lane == 0 && tot != prev) atomicAdd(&shist[kk + 1], tot - prev);
         prev = tot;
@@ -305,9 +325,9 @@ static cudaError_t launch_ka(const CoverArgs& a, cudaStream_t s)
 
 cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s)
 {
-    // 16-bit queue entries hold rounds < 64 and 16-bit counters a lane's sum of
-    // at most 32 per word: at most 64 words per lane per CTA
-    if (2ull * a.cta_words > 64ull * 256) return cudaErrorInvalidValue;
+    // 10-bit counters hold a lane's sum of at most 32 per word over its words
+    // of a CTA (and 16-bit queue entries hold rounds < 64)
+    if (2ull * a.cta_words > (unsigned long long)kMaxWordsPerLane * 256) return cudaErrorInvalidValue;
     switch (KA) {
     case 32: return launch_ka<32>(a, s);
     case 48: return launch_ka<48>(a, s);
