@@ -545,7 +545,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
         if (KA && ctx->ka_override && (uint32_t)ctx->ka_override <= K1) KA = ctx->ka_override;
         ctx->prof_begin(kProfCover, n_count);
-        if (KA) GB_CUDA(gb::launch_cover_fast(ca, ctx->retry_count.as<unsigned int>() + 2, KA, s));
+        if (KA) GB_CUDA(gb::launch_cover_fast(ca, KA, s));
         else GB_CUDA(gb::launch_cover(ca, (int)cfg.cta_threads, s));
         ctx->prof_end();
 

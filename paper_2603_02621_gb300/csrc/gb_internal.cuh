@@ -132,7 +132,7 @@ cudaError_t launch_cover(const CoverArgs& a, int threads, cudaStream_t s);
 // generic kernel in max-only mode fills it in for segments where nothing else
 // set a key).
 int cover_fast_phase_primes(uint32_t K, uint64_t n_hi);   // KA for K primes near n_hi (0: none)
-cudaError_t launch_cover_fast(const CoverArgs& a, unsigned int* chunk_ctr /*device*/, int KA, cudaStream_t s);
+cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s);
 
 struct RetryArgs {
     const uint64_t* Q;
