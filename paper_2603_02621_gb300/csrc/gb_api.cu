@@ -358,7 +358,7 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     if (const char* e = getenv("GB_COVER")) ctx->generic_cover = std::string(e) == "generic";
     if (const char* e = getenv("GB_KA")) {
         const int v = atoi(e);
-        if (v == 32 || v == 48 || v == 64 || v == 96 || v == 128) ctx->ka_override = v;
+        if (v == 64 || v == 128 || v == 192 || v == 256) ctx->ka_override = v;
     }
     rc = build_primes(ctx);
     if (rc) {
@@ -544,6 +544,11 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         // writes it) or the pass has too few primes for its first phase
         int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
         if (KA && ctx->ka_override && (uint32_t)ctx->ka_override <= K1) KA = ctx->ka_override;
+        if (KA) {
+            // the two-phase kernel keeps two lists of the CTA's words in shared memory
+            ca.cta_words = std::min<uint32_t>(1024, (uint32_t)(S / 64));
+            ca.chunks_per_seg = (uint32_t)((S / 64 + ca.cta_words - 1) / ca.cta_words);
+        }
         ctx->prof_begin(kProfCover, n_count);
         if (KA) GB_CUDA(gb::launch_cover_fast(ca, KA, s));
         else GB_CUDA(gb::launch_cover(ca, (int)cfg.cta_threads, s));

@@ -5,28 +5,28 @@
 // smaller p covered gets p_min(n) = p (GoldbachGPU, arXiv 2603.02621, Sec.
 // 2.3.1-2.3.2, in the bitwise form of Sec. 4.3).  Only the schedule differs.
 //
-// Phase A (k_cover_fast).  Most n are covered by one of the first few dozen
-// primes, so the first KA odd primes are applied to every coverage word
-// unconditionally, with the loop unrolled at compile time.  A lane owns one
-// 32-bit word of C (32 even n).  With the halo chosen so that d_3 = (H - 4)/2
-// is a multiple of 32, the partner bits of word w for the prime p start at bit
-// 32(w + d_3/32) - (p-3)/2 of Q: the word offset and the shift of every step
-// are compile-time constants, and the few Q words a lane needs sit in
-// registers.  A step is then
+// Unrolled blocks.  Most n are covered by one of the first few dozen primes,
+// so primes are applied in blocks of 64, unrolled at compile time.  A lane owns
+// one 32-bit word of C (32 even n).  With the halo chosen so that
+// d_3 = (H - 4)/2 is a multiple of 32, the partner bits of word w for the
+// prime p start at bit 32(w + d_3/32) - (p-3)/2 of Q: the word offset and the
+// shift of every step are compile-time constants, and the few Q words a lane
+// needs sit in registers.  A step is then
 //     s = funnel-shift of two window registers,  C |= s,  cum_k += popc(C)
-// and the histogram of the first phase follows from the cumulative counts:
-// #{n : p_min(n) = p_k} = cum_k - cum_{k-1}.
+// and the histogram follows from the cumulative counts:
+// #{n : p_min(n) = p_k} = cum_k - cum_{k-1}.  The first block runs on every
+// word of the CTA; the words it leaves open (about one in five near 1e10) are
+// compacted in shared memory and the next block runs on those alone, so every
+// lane of every step still works on an open word.
 //
-// Phase B, in the same kernel while the CTA's part of Q is still in L1.  After
-// each round of the first phase, the warp takes the n left open one at a time:
-// lane t probes the bit of Q at j + d_k for k = KA + t (32 consecutive primes
-// per step, a few cache lines), and the lowest set bit of the ballot is the
-// minimal prime.  Most open n are settled in one step.  An n still open after
-// K primes goes to the retry pass (or counts as unresolved).
+// Probing.  The few n open after the last block (about 1 in 10^5 near 1e10)
+// are taken one at a time by a warp: lane t probes the bit of Q at j + d_k for
+// k = k0 + t, and the lowest set bit of the ballot is p_min.  An n still open
+// after K primes goes to the retry pass (or counts as unresolved).
 //
-// The largest p_min of a segment, with its smallest n, comes from phase B (or
-// the retry pass).  A segment where no n needed more than KA primes gets its
-// maximum from the generic kernel run in max-only mode.
+// The largest p_min of a segment, with its smallest n, comes from the probing
+// (or the retry pass).  A segment where no n outlived the unrolled blocks gets
+// its maximum from the generic kernel run in max-only mode.
 #include <utility>
 
 #include "gb_internal.cuh"
@@ -48,12 +48,6 @@ __host__ __device__ constexpr uint32_t odd_prime(int k)
     return c;
 }
 
-// window registers needed for KA primes: R[t] = Q32[base - t], t <= (e+31)/32
-__host__ __device__ constexpr int window_regs(int KA)
-{
-    return (int)(((odd_prime(KA - 1) - 3) / 2 + 31) / 32) + 1;
-}
-
 // cumulative counts are kept three per register (10-bit fields): a lane adds
 // at most 32 per word and handles at most 31 words per CTA (32 * 31 < 2^10)
 constexpr int kCumBits = 10;
@@ -61,41 +55,175 @@ constexpr uint32_t kCumMask = (1u << kCumBits) - 1;
 constexpr int kMaxWordsPerLane = 31;
 __host__ __device__ constexpr int cum_regs(int KA) { return (KA + 2) / 3; }
 
-template <int K, int NR, int KH>
-__device__ __forceinline__ void phase_a_step(const uint32_t (&R)[NR], uint32_t& C, uint32_t (&cum)[KH])
+// ---------------------------------------------------------------------------
+// one unrolled block of 64 primes: indices K0 .. K0+63, window registers
+// R[t] = Q32[base - C0 - t] with C0 = the first block step's word offset - 1
+// ---------------------------------------------------------------------------
+constexpr int kBlock = 64;
+
+__host__ __device__ constexpr uint32_t step_e(int k) { return (odd_prime(k) - 3) / 2; }
+__host__ __device__ constexpr int block_c0(int K0)
 {
-    constexpr uint32_t e = (odd_prime(K) - 3) / 2;    // bit distance from p = 3
-    constexpr uint32_t c = (e + 31) / 32;
+    return K0 == 0 ? 0 : (int)((step_e(K0) + 31) / 32) - 1;
+}
+__host__ __device__ constexpr int block_regs(int K0)
+{
+    return (int)((step_e(K0 + kBlock - 1) + 31) / 32) - block_c0(K0) + 1;
+}
+
+template <int K, int K0, int NR, int KH>
+__device__ __forceinline__ void block_step(const uint32_t (&R)[NR], uint32_t& C, uint32_t (&cum)[KH])
+{
+    constexpr uint32_t e = step_e(K);
+    constexpr int c = (int)((e + 31) / 32);
     constexpr uint32_t sh = 32 * c - e;
-    static_assert(c < (uint32_t)NR, "window too small");
+    constexpr int r = c - block_c0(K0);
+    static_assert(r >= 0 && r < NR, "window too small");
     uint32_t s;
-    if constexpr (sh == 0) s = R[c];
-    else s = __funnelshift_r(R[c], R[c - 1], sh);
+    if constexpr (sh == 0) s = R[r];
+    else s = __funnelshift_r(R[r], R[r - 1], sh);
     C |= s;
-    if constexpr (K % 3 == 0) cum[K / 3] += __popc(C);
-    else cum[K / 3] += __popc(C) << (kCumBits * (K % 3));
+    constexpr int j = K - K0;
+    if constexpr (j % 3 == 0) cum[j / 3] += __popc(C);
+    else cum[j / 3] += __popc(C) << (kCumBits * (j % 3));
 }
 
-template <int NR, int KH, int... K>
-__device__ __forceinline__ void phase_a(std::integer_sequence<int, K...>, const uint32_t (&R)[NR], uint32_t& C,
-                                        uint32_t (&cum)[KH])
+template <int K0, int NR, int KH, int... J>
+__device__ __forceinline__ void run_block(std::integer_sequence<int, J...>, const uint32_t (&R)[NR], uint32_t& C,
+                                          uint32_t (&cum)[KH])
 {
-    (phase_a_step<K, NR, KH>(R, C, cum), ...);
+    (block_step<K0 + J, K0, NR, KH>(R, C, cum), ...);
 }
 
-// Second phase, warp-wide: the 32 lanes probe 32 consecutive primes for one
-// open n at a time; their partner bits lie within a few words of Q, so a step
-// costs one or two cache lines, and the first set bit of the ballot is p_min.
-template <int NT, int KA>
-__global__ void __launch_bounds__(NT, KA <= 64 ? 4 : 3) k_cover_fast(const CoverArgs a)
+// add one block's histogram (cumulative counts, warp-reduced) to shist
+template <int K0, int KH>
+__device__ __forceinline__ void flush_block(const uint32_t (&cum)[KH], uint32_t init_pop, uint32_t* shist, int lane)
+{
+    uint32_t prev = __reduce_add_sync(0xffffffffu, init_pop);
+#pragma unroll
+    for (int j = 0; j < kBlock; ++j) {
+        const uint32_t v = (cum[j / 3] >> (kCumBits * (j % 3))) & kCumMask;
+        const uint32_t tot = __reduce_add_sync(0xffffffffu, v);
+        if (lane == 0 && tot != prev) atomicAdd(&shist[K0 + j + 1], tot - prev);
+        prev = tot;
+    }
+}
+
+// Block b > 0 over the compacted words of list `in` (n_in entries); words
+// still open are appended to `out`.  Entries: word (CTA-relative) and C.
+template <int NT, int K0>
+__device__ __forceinline__ void later_block(const uint32_t* Qc, uint32_t D0w, const uint32_t* in_w,
+                                            const uint32_t* in_c, uint32_t n_in, uint32_t* out_w, uint32_t* out_c,
+                                            uint32_t* n_out, uint32_t* shist, uint32_t& nsteps)
+{
+    constexpr int NR = block_regs(K0);
+    constexpr int KH = (kBlock + 2) / 3;
+    constexpr int C0 = block_c0(K0);
+    const int lane = threadIdx.x & 31;
+    uint32_t cum[KH];
+#pragma unroll
+    for (int j = 0; j < KH; ++j) cum[j] = 0;
+    uint32_t init_pop = 0;
+    for (uint32_t b = threadIdx.x - lane; b < n_in; b += NT) {
+        const uint32_t e = b + lane;
+        const bool active = e < n_in;
+        uint32_t C = 0xffffffffu, wrel = 0;
+        uint32_t R[NR];
+        if (active) {
+            wrel = in_w[e];
+            C = in_c[e];
+#pragma unroll
+            for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - C0 - t);
+        } else {
+#pragma unroll
+            for (int t = 0; t < NR; ++t) R[t] = 0;
+        }
+        init_pop += __popc(C);
+        nsteps += active ? kBlock : 0;
+        run_block<K0, NR, KH>(std::make_integer_sequence<int, kBlock>{}, R, C, cum);
+        if (C != 0xffffffffu) {
+            const uint32_t slot = atomicAdd(n_out, 1u);
+            out_w[slot] = wrel;
+            out_c[slot] = C;
+        }
+    }
+    flush_block<K0, KH>(cum, init_pop, shist, lane);
+}
+
+// Phase B over a list of open words: the warp takes the open n one at a time,
+// lane t probing the prime k + t; the lowest set bit of the ballot is p_min.
+template <int NT>
+__device__ __forceinline__ void probe_open(const CoverArgs& a, const uint32_t* Qc, const uint32_t* sd,
+                                           const uint32_t* in_w, const uint32_t* in_c, uint32_t n_in,
+                                           uint32_t k_first, uint64_t w_begin, uint32_t j_cta, uint32_t seg,
+                                           uint32_t* shist, unsigned long long& best, uint32_t& nsteps)
 {
     constexpr int NW = NT / 32;
-    constexpr int NR = window_regs(KA);
-    constexpr int KH = cum_regs(KA);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t e = warp; e < n_in; e += NW) {
+        const uint32_t wrel = in_w[e];
+        uint32_t mm = ~in_c[e];
+        while (mm) {
+            const uint32_t b = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint32_t rel = 32 * wrel + b;              // CTA-relative n index
+            uint32_t k = k_first;
+            for (;;) {
+                const uint32_t kt = k + (uint32_t)lane;
+                uint32_t bit = 0;
+                if (kt < a.K) {
+                    const uint32_t i = rel + sd[kt];
+                    bit = (__ldg(Qc + (i >> 5)) >> (i & 31)) & 1u;
+                }
+                const unsigned hb = __ballot_sync(0xffffffffu, bit);
+                if (lane == 0) nsteps += 32;
+                if (hb) {
+                    const uint32_t kk = k + (__ffs(hb) - 1);
+                    if (lane == 0) {
+                        atomicAdd(&shist[kk + 1], 1u);
+                        const unsigned long long key =
+                            ((unsigned long long)(kk + 2) << 32) | (0xffffffffull - (j_cta + rel));
+                        if (key > best) best = key;
+                    }
+                    break;
+                }
+                k += 32;
+                if (k >= a.K) {
+                    // open after every prime of this pass
+                    if (lane == 0) {
+                        const uint64_t jn = 32 * w_begin + rel;          // slab-relative n index
+                        bool queued = false;
+                        if (a.retry) {
+                            const unsigned int slot = atomicAdd(a.retry_count, 1u);
+                            if (slot < a.retry_cap) {
+                                a.retry[slot].w = jn >> 6;
+                                a.retry[slot].C = ~(1ull << (jn & 63));
+                                queued = true;
+                            }
+                        }
+                        if (!queued) atomicAdd(&a.unresolved[seg], 1ull);
+                    }
+                    break;
+                }
+            }
+        }
+    }
+}
+
+// NB unrolled blocks of 64 primes (the first over every word, the later ones
+// over the words still open), then per-n probing
+template <int NT, int NB>
+__global__ void __launch_bounds__(NT, 3) k_cover_fast(const CoverArgs a)
+{
+    constexpr int NW = NT / 32;
+    constexpr int NR = block_regs(0);
+    constexpr int KH = (kBlock + 2) / 3;
     extern __shared__ uint32_t smem[];
     uint32_t* sd = smem;                                    // d_k for the K odd primes
     uint32_t* shist = sd + a.K;                             // K + 1 counters
+    uint32_t* lists = shist + a.K + 1;                      // 2 lists x (words, C), cta words each
     __shared__ unsigned long long smax;
+    __shared__ uint32_t counts[2];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -109,10 +237,13 @@ __global__ void __launch_bounds__(NT, KA <= 64 ? 4 : 3) k_cover_fast(const Cover
     const uint64_t n_words32 = (a.n_count + 31) / 32;
     if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
     if (w_end > n_words32) w_end = n_words32;
+    const uint32_t cap = 2 * a.cta_words;                   // list capacity: every word of the CTA
+    uint32_t* lw[2] = {lists, lists + 2 * cap};
+    uint32_t* lc[2] = {lists + cap, lists + 3 * cap};
 
     for (uint32_t k = threadIdx.x; k < a.K; k += NT) sd[k] = (a.H - a.primes[1 + k] - 1) >> 1;
     for (uint32_t k = threadIdx.x; k <= a.K; k += NT) shist[k] = 0;
-    if (threadIdx.x == 0) smax = 0;
+    if (threadIdx.x == 0) { smax = 0; counts[0] = 0; counts[1] = 0; }
     __syncthreads();
 
     const uint32_t* Qc = reinterpret_cast<const uint32_t*>(a.Q) + w_begin;   // CTA-relative words
@@ -122,103 +253,73 @@ __global__ void __launch_bounds__(NT, KA <= 64 ? 4 : 3) k_cover_fast(const Cover
     const uint32_t n_rel_end = (uint32_t)(n_left < 32ull * nw_cta ? n_left : 32ull * nw_cta);
     const uint32_t j_cta = (uint32_t)(32 * (w_begin - seg_w0));   // segment-relative n of the CTA's first n
 
-    uint32_t cum[KH];
+    uint32_t nsteps = 0;
+    // block 0 over every word
+    {
+        uint32_t cum[KH];
 #pragma unroll
-    for (int k = 0; k < KH; ++k) cum[k] = 0;
-    uint32_t init_pop = 0, nwords = 0, nsteps = 0;
-    unsigned long long best = 0;                            // lane 0 only
-
-    for (uint32_t wbase = 32 * warp; wbase < nw_cta; wbase += 32 * NW) {
-        const uint32_t wrel = wbase + lane;
-        const bool active = wrel < nw_cta;
-        uint32_t C = 0xffffffffu;
-        uint32_t R[NR];
-        if (active) {
-            C = 0;
-            const uint32_t j0 = 32 * wrel;
-            if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);   // past the slab end
-            if (a.has_n4 && w_begin + wrel == 0) {
-                C |= 1u;                                     // n = 4 = 2 + 2
-                atomicAdd(&shist[0], 1u);
-            }
-#pragma unroll
-            for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - t);
-        } else {
-#pragma unroll
-            for (int t = 0; t < NR; ++t) R[t] = 0;
-        }
-        init_pop += __popc(C);
-        nwords += active;
-        phase_a<NR, KH>(std::make_integer_sequence<int, KA>{}, R, C, cum);
-
-        // second phase for the n this round left open, one n at a time
-        const uint32_t m = ~C;
-        unsigned lanes = __ballot_sync(0xffffffffu, m != 0);
-        while (lanes) {
-            const int src = __ffs(lanes) - 1;
-            lanes &= lanes - 1;
-            uint32_t mm = __shfl_sync(0xffffffffu, m, src);
-            while (mm) {
-                const uint32_t b = __ffs(mm) - 1;
-                mm &= mm - 1;
-                const uint32_t rel = 32 * (wbase + (uint32_t)src) + b;   // CTA-relative n index
-                uint32_t k = KA;
-                for (;;) {
-                    const uint32_t kt = k + (uint32_t)lane;
-                    uint32_t bit = 0;
-                    if (kt < a.K) {
-                        const uint32_t i = rel + sd[kt];
-                        bit = (__ldg(Qc + (i >> 5)) >> (i & 31)) & 1u;
-                    }
-                    const unsigned hb = __ballot_sync(0xffffffffu, bit);
-                    ++nsteps;
-                    if (hb) {
-                        const uint32_t kk = k + (__ffs(hb) - 1);
-                        if (lane == 0) {
-                            atomicAdd(&shist[kk + 1], 1u);
-                            const unsigned long long key =
-                                ((unsigned long long)(kk + 2) << 32) | (0xffffffffull - (j_cta + rel));
-                            if (key > best) best = key;
-                        }
-                        break;
-                    }
-                    k += 32;
-                    if (k >= a.K) {
-                        // open after every prime of this pass
-                        if (lane == 0) {
-                            const uint64_t jn = 32 * w_begin + rel;          // slab-relative n index
-                            bool queued = false;
-                            if (a.retry) {
-                                const unsigned int slot = atomicAdd(a.retry_count, 1u);
-                                if (slot < a.retry_cap) {
-                                    a.retry[slot].w = jn >> 6;
-                                    a.retry[slot].C = ~(1ull << (jn & 63));
-                                    queued = true;
-                                }
-                            }
-                            if (!queued) atomicAdd(&a.unresolved[seg], 1ull);
-                        }
-                        break;
-                    }
+        for (int k = 0; k < KH; ++k) cum[k] = 0;
+        uint32_t init_pop = 0;
+        for (uint32_t wbase = 32 * warp; wbase < nw_cta; wbase += 32 * NW) {
+            const uint32_t wrel = wbase + lane;
+            const bool active = wrel < nw_cta;
+            uint32_t C = 0xffffffffu;
+            uint32_t R[NR];
+            if (active) {
+                C = 0;
+                const uint32_t j0 = 32 * wrel;
+                if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);   // past the slab end
+                if (a.has_n4 && w_begin + wrel == 0) {
+                    C |= 1u;                                     // n = 4 = 2 + 2
+                    atomicAdd(&shist[0], 1u);
                 }
+#pragma unroll
+                for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - t);
+            } else {
+#pragma unroll
+                for (int t = 0; t < NR; ++t) R[t] = 0;
+            }
+            init_pop += __popc(C);
+            nsteps += active ? kBlock : 0;
+            run_block<0, NR, KH>(std::make_integer_sequence<int, kBlock>{}, R, C, cum);
+            if (C != 0xffffffffu) {
+                const uint32_t slot = atomicAdd(&counts[0], 1u);
+                lw[0][slot] = wrel;
+                lc[0][slot] = C;
             }
         }
+        flush_block<0, KH>(cum, init_pop, shist, lane);
     }
+    __syncthreads();
+    int cur = 0;
+    if constexpr (NB >= 2) {
+        later_block<NT, 64>(Qc, D0w, lw[0], lc[0], counts[0], lw[1], lc[1], &counts[1], shist, nsteps);
+        __syncthreads();
+        if (threadIdx.x == 0) counts[0] = 0;
+        cur = 1;
+        __syncthreads();
+    }
+    if constexpr (NB >= 3) {
+        later_block<NT, 128>(Qc, D0w, lw[1], lc[1], counts[1], lw[0], lc[0], &counts[0], shist, nsteps);
+        __syncthreads();
+        if (threadIdx.x == 0) counts[1] = 0;
+        cur = 0;
+        __syncthreads();
+    }
+    if constexpr (NB >= 4) {
+        later_block<NT, 192>(Qc, D0w, lw[0], lc[0], counts[0], lw[1], lc[1], &counts[1], shist, nsteps);
+        __syncthreads();
+        cur = 1;
+    }
+    unsigned long long best = 0;                            // lane 0 of each warp
+    probe_open<NT>(a, Qc, sd, lw[cur], lc[cur], counts[cur], (uint32_t)(kBlock * NB), w_begin, j_cta, seg, shist,
+                   best, nsteps);
 
     if (a.iters) {
-        // first-phase word steps plus second-phase probes (32 per warp step)
-        unsigned long long t = (unsigned long long)nwords * KA + (lane == 0 ? 32ull * nsteps : 0ull);
+        // unrolled word steps plus probes
+        unsigned long long t = nsteps;
         for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0 && t) atomicAdd(a.iters, t);
-    }
-    // first-phase histogram from the cumulative counts
-    uint32_t prev = __reduce_add_sync(0xffffffffu, init_pop);
-#pragma unroll
-    for (int kk = 0; kk < KA; ++kk) {
-        const uint32_t v = (cum[kk / 3] >> (kCumBits * (kk % 3))) & kCumMask;
-        const uint32_t tot = __reduce_add_sync(0xffffffffu, v);
-        if (lane == 0 && tot != prev) atomicAdd(&shist[kk + 1], tot - prev);
-        prev = tot;
     }
     if (lane == 0 && best) atomicMax(&smax, best);
     __syncthreads();
@@ -230,25 +331,21 @@ __global__ void __launch_bounds__(NT, KA <= 64 ? 4 : 3) k_cover_fast(const Cover
 
 int cover_fast_phase_primes(uint32_t K, uint64_t n_hi)
 {
-    // first-phase length by magnitude: the share of n still open after KA
-    // primes grows with log n (about 0.6% after 64 primes near 1e10, 0.6%
-    // after 128 near 4e18), and a second-phase probe costs several first-phase
-    // steps' worth of work per n
-    int want = n_hi < 1000000000ull ? 48 : n_hi < 100000000000ull ? 64 : n_hi < 100000000000000ull ? 96 : 128;
-    const int opts[5] = {128, 96, 64, 48, 32};
-    for (int o : opts)
-        if (o <= want && (uint32_t)o <= K) return o;
-    return 0;
+    // unrolled blocks of 64 primes, by magnitude: the share of n still open
+    // after 64 primes is about 0.6% near 1e10, 1.5% near 1e12 and 6% near 4e18
+    int nb = n_hi < 100000000000ull ? 2 : n_hi < 10000000000000000ull ? 3 : 4;
+    while (nb > 0 && (uint32_t)(kBlock * nb) > K) --nb;
+    return kBlock * nb;
 }
 
-template <int KA>
-static cudaError_t launch_ka(const CoverArgs& a, cudaStream_t s)
+template <int NB>
+static cudaError_t launch_nb(const CoverArgs& a, cudaStream_t s)
 {
     constexpr int NT = 256;
     const unsigned grid = a.nseg * a.chunks_per_seg;
     if (grid == 0) return cudaSuccess;
-    const size_t smem = (size_t)(2 * a.K + 1) * 4;
-    auto k = k_cover_fast<NT, KA>;
+    const size_t smem = (size_t)(2 * a.K + 1 + 8 * a.cta_words) * 4;
+    auto k = k_cover_fast<NT, NB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, smem, s>>>(a);
@@ -261,11 +358,10 @@ cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s)
     // of a CTA
     if (2ull * a.cta_words > (unsigned long long)kMaxWordsPerLane * 256) return cudaErrorInvalidValue;
     switch (KA) {
-    case 32: return launch_ka<32>(a, s);
-    case 48: return launch_ka<48>(a, s);
-    case 64: return launch_ka<64>(a, s);
-    case 96: return launch_ka<96>(a, s);
-    case 128: return launch_ka<128>(a, s);
+    case 64: return launch_nb<1>(a, s);
+    case 128: return launch_nb<2>(a, s);
+    case 192: return launch_nb<3>(a, s);
+    case 256: return launch_nb<4>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }
