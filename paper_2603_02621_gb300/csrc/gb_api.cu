@@ -575,23 +575,9 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
             ctx->prof_end();
         }
 
-        if (KA) {
-            // maxima of segments that neither the second phase nor the retry pass reached
-            gb::CoverArgs mx = ca;
-            mx.max_only = 1;
-            mx.maxkey_check = ca.maxkey;
-            mx.maxkey = ctx->maxkey2.as<unsigned long long>();
-            mx.pmin = nullptr;
-            mx.retry = nullptr;
-            mx.iters = nullptr;
-            ctx->prof_begin(kProfReduce, ns);
-            GB_CUDA(gb::launch_cover(mx, (int)cfg.cta_threads, s));
-            ctx->prof_end();
-        }
-
         gb::ReduceArgs rd{};
         rd.nseg = (uint32_t)ns;
-        rd.maxkey2 = KA ? ctx->maxkey2.as<unsigned long long>() : nullptr;
+        rd.maxkey2 = nullptr;
         rd.hist_stride = hist_stride;
         rd.hist = ca.hist;
         rd.maxkey = ca.maxkey;

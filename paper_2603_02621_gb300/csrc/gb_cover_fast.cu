@@ -24,9 +24,11 @@
 // k = k0 + t, and the lowest set bit of the ballot is p_min.  An n still open
 // after K primes goes to the retry pass (or counts as unresolved).
 //
-// The largest p_min of a segment, with its smallest n, comes from the probing
-// (or the retry pass).  A segment where no n outlived the unrolled blocks gets
-// its maximum from the generic kernel run in max-only mode.
+// The largest p_min of a CTA's words, with its smallest n, comes from the
+// probing when any n reached it; otherwise the last block that ran holds it,
+// and that block is run once more over its input words, recording for each
+// word the last step that set a bit.
+#include <type_traits>
 #include <utility>
 
 #include "gb_internal.cuh"
@@ -150,6 +152,59 @@ __device__ __forceinline__ void later_block(const uint32_t* Qc, uint32_t D0w, co
     flush_block<K0, KH>(cum, init_pop, shist, lane);
 }
 
+// Re-run block K0 over its input list recording, per word, the last step that
+// set a bit and the lowest bit it set: the largest p_min among the list's
+// words, with its smallest n.  Used when no n of the CTA outlived the blocks.
+template <int K, int K0, int NR>
+__device__ __forceinline__ void track_step(const uint32_t (&R)[NR], uint32_t& C, uint32_t& last, uint32_t& lastbits)
+{
+    constexpr uint32_t e = step_e(K);
+    constexpr int c = (int)((e + 31) / 32);
+    constexpr uint32_t sh = 32 * c - e;
+    constexpr int r = c - block_c0(K0);
+    uint32_t s;
+    if constexpr (sh == 0) s = R[r];
+    else s = __funnelshift_r(R[r], R[r - 1], sh);
+    const uint32_t nw = s & ~C;
+    C |= s;
+    if (nw) { last = K + 1; lastbits = nw; }
+}
+
+template <int K0, int NR, int... J>
+__device__ __forceinline__ void track_block_steps(std::integer_sequence<int, J...>, const uint32_t (&R)[NR],
+                                                  uint32_t& C, uint32_t& last, uint32_t& lastbits)
+{
+    (track_step<K0 + J, K0, NR>(R, C, last, lastbits), ...);
+}
+
+template <int NT, int K0>
+__device__ __forceinline__ unsigned long long track_block(const uint32_t* Qc, uint32_t D0w, const uint32_t* in_w,
+                                                          const uint32_t* in_c, uint32_t n_in, uint32_t j_cta)
+{
+    constexpr int NR = block_regs(K0);
+    constexpr int C0 = block_c0(K0);
+    const int lane = threadIdx.x & 31;
+    unsigned long long best = 0;
+    for (uint32_t b = threadIdx.x - lane; b < n_in; b += NT) {
+        const uint32_t e = b + lane;
+        if (e >= n_in) break;
+        const uint32_t wrel = in_w[e];
+        uint32_t C = in_c[e];
+        uint32_t R[NR];
+#pragma unroll
+        for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - C0 - t);
+        uint32_t last = 0, lastbits = 0;
+        track_block_steps<K0, NR>(std::make_integer_sequence<int, kBlock>{}, R, C, last, lastbits);
+        if (last) {
+            // prime index of step K is K + 1 (index 0 is the prime 2): key holds index + 1
+            const uint32_t j = j_cta + 32 * wrel + (__ffs(lastbits) - 1);
+            const unsigned long long key = ((unsigned long long)(last + 1) << 32) | (0xffffffffull - j);
+            if (key > best) best = key;
+        }
+    }
+    return best;
+}
+
 // Phase B over a list of open words: the warp takes the open n one at a time,
 // lane t probing the prime k + t; the lowest set bit of the ballot is p_min.
 template <int NT>
@@ -213,7 +268,7 @@ __device__ __forceinline__ void probe_open(const CoverArgs& a, const uint32_t* Q
 // NB unrolled blocks of 64 primes (the first over every word, the later ones
 // over the words still open), then per-n probing
 template <int NT, int NB>
-__global__ void __launch_bounds__(NT, 3) k_cover_fast(const CoverArgs a)
+__global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
 {
     constexpr int NW = NT / 32;
     constexpr int NR = block_regs(0);
@@ -238,8 +293,9 @@ __global__ void __launch_bounds__(NT, 3) k_cover_fast(const CoverArgs a)
     if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
     if (w_end > n_words32) w_end = n_words32;
     const uint32_t cap = 2 * a.cta_words;                   // list capacity: every word of the CTA
-    uint32_t* lw[2] = {lists, lists + 2 * cap};
-    uint32_t* lc[2] = {lists + cap, lists + 3 * cap};
+    // list i: words at lists + 2*cap*i, coverage right after them
+    auto lw = [&](int i) { return lists + 2 * cap * (uint32_t)i; };
+    auto lc = [&](int i) { return lists + 2 * cap * (uint32_t)i + cap; };
 
     for (uint32_t k = threadIdx.x; k < a.K; k += NT) sd[k] = (a.H - a.primes[1 + k] - 1) >> 1;
     for (uint32_t k = threadIdx.x; k <= a.K; k += NT) shist[k] = 0;
@@ -284,36 +340,79 @@ __global__ void __launch_bounds__(NT, 3) k_cover_fast(const CoverArgs a)
             run_block<0, NR, KH>(std::make_integer_sequence<int, kBlock>{}, R, C, cum);
             if (C != 0xffffffffu) {
                 const uint32_t slot = atomicAdd(&counts[0], 1u);
-                lw[0][slot] = wrel;
-                lc[0][slot] = C;
+                lw(0)[slot] = wrel;
+                lc(0)[slot] = C;
             }
         }
         flush_block<0, KH>(cum, init_pop, shist, lane);
     }
     __syncthreads();
-    int cur = 0;
-    if constexpr (NB >= 2) {
-        later_block<NT, 64>(Qc, D0w, lw[0], lc[0], counts[0], lw[1], lc[1], &counts[1], shist, nsteps);
+    // later blocks over the words still open.  The lists alternate: a block
+    // reads one and writes the other, and a block with no input writes
+    // nothing, so the input list of the last block that ran stays intact.
+    int cur = 0;                      // list holding the words still open
+    uint32_t n_cur = counts[0];
+    int last_in = 0;                  // last block that ran (0: block 0, input = every word)
+    int last_list = 0;                // its input list (later blocks)
+    uint32_t last_n = 0;              // and that list's length
+    auto run_later = [&](auto k0_tag) {
+        constexpr int K0 = decltype(k0_tag)::value;
+        if (n_cur == 0) return;
+        const int out = cur ^ 1;
+        if (threadIdx.x == 0) counts[out] = 0;
         __syncthreads();
-        if (threadIdx.x == 0) counts[0] = 0;
-        cur = 1;
+        later_block<NT, K0>(Qc, D0w, lw(cur), lc(cur), n_cur, lw(out), lc(out), &counts[out], shist, nsteps);
         __syncthreads();
-    }
-    if constexpr (NB >= 3) {
-        later_block<NT, 128>(Qc, D0w, lw[1], lc[1], counts[1], lw[0], lc[0], &counts[0], shist, nsteps);
-        __syncthreads();
-        if (threadIdx.x == 0) counts[1] = 0;
-        cur = 0;
-        __syncthreads();
-    }
-    if constexpr (NB >= 4) {
-        later_block<NT, 192>(Qc, D0w, lw[0], lc[0], counts[0], lw[1], lc[1], &counts[1], shist, nsteps);
-        __syncthreads();
-        cur = 1;
-    }
+        last_in = K0 / kBlock;
+        last_list = cur;
+        last_n = n_cur;
+        cur = out;
+        n_cur = counts[out];
+    };
+    if constexpr (NB >= 2) run_later(std::integral_constant<int, 64>{});
+    if constexpr (NB >= 3) run_later(std::integral_constant<int, 128>{});
+    if constexpr (NB >= 4) run_later(std::integral_constant<int, 192>{});
+
     unsigned long long best = 0;                            // lane 0 of each warp
-    probe_open<NT>(a, Qc, sd, lw[cur], lc[cur], counts[cur], (uint32_t)(kBlock * NB), w_begin, j_cta, seg, shist,
+    probe_open<NT>(a, Qc, sd, lw(cur), lc(cur), n_cur, (uint32_t)(kBlock * NB), w_begin, j_cta, seg, shist,
                    best, nsteps);
+    if (lane == 0 && best) atomicMax(&smax, best);
+    __syncthreads();
+    if (smax == 0) {
+        // no n outlived the blocks with a prime found: the maximum is in the
+        // last block that ran, among that block's input words
+        if (last_in == 0) {
+            // block 0's input is every word of the CTA: rebuild it (both lists
+            // are free: block 0 left no open word)
+            for (uint32_t w = threadIdx.x; w < nw_cta; w += NT) {
+                uint32_t C = 0;
+                const uint32_t j0 = 32 * w;
+                if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);
+                if (a.has_n4 && w_begin + w == 0) C |= 1u;
+                lw(1)[w] = w;
+                lc(1)[w] = C;
+            }
+            __syncthreads();
+            best = track_block<NT, 0>(Qc, D0w, lw(1), lc(1), nw_cta, j_cta);
+            if (a.has_n4 && w_begin == 0 && threadIdx.x == 0) {
+                // n = 4 (p_min 2, prime index 0) if nothing larger was found
+                const unsigned long long k4 = (1ull << 32) | 0xffffffffull;
+                if (k4 > best) best = k4;
+            }
+        } else if (NB >= 2 && last_in == 1) {
+            best = track_block<NT, (NB >= 2 ? 64 : 0)>(Qc, D0w, lw(last_list), lc(last_list), last_n, j_cta);
+        } else if (NB >= 3 && last_in == 2) {
+            best = track_block<NT, (NB >= 3 ? 128 : 0)>(Qc, D0w, lw(last_list), lc(last_list), last_n, j_cta);
+        } else if (NB >= 4 && last_in == 3) {
+            best = track_block<NT, (NB >= 4 ? 192 : 0)>(Qc, D0w, lw(last_list), lc(last_list), last_n, j_cta);
+        }
+        const uint32_t khi = (uint32_t)(best >> 32);
+        const uint32_t mhi = __reduce_max_sync(0xffffffffu, khi);
+        const uint32_t klo = khi == mhi ? (uint32_t)best : 0u;
+        const uint32_t mlo = __reduce_max_sync(0xffffffffu, klo);
+        if (lane == 0 && mhi) atomicMax(&smax, ((unsigned long long)mhi << 32) | mlo);
+        __syncthreads();
+    }
 
     if (a.iters) {
         // unrolled word steps plus probes
@@ -321,8 +420,6 @@ __global__ void __launch_bounds__(NT, 3) k_cover_fast(const CoverArgs a)
         for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0 && t) atomicAdd(a.iters, t);
     }
-    if (lane == 0 && best) atomicMax(&smax, best);
-    __syncthreads();
     uint32_t* hrow = a.hist + (uint64_t)seg * a.hist_stride;
     for (uint32_t kk = threadIdx.x; kk <= a.K; kk += NT)
         if (shist[kk]) atomicAdd(&hrow[kk], shist[kk]);

@@ -125,12 +125,10 @@ struct CoverArgs {
 };
 cudaError_t launch_cover(const CoverArgs& a, int threads, cudaStream_t s);
 
-// Two-phase cover (k_cover_fast): the first KA odd primes on every 32-bit
-// coverage word, unrolled; then, in the same kernel, each n still open probes
-// the primes KA+1 .. K in order.  Needs K >= KA, H = 4 (mod 64) and no p_min
-// array; does not record the maximum of words closed in the first phase (the
-// generic kernel in max-only mode fills it in for segments where nothing else
-// set a key).
+// Block cover (k_cover_fast): unrolled blocks of 64 primes, the first over
+// every 32-bit coverage word, each later one over the words still open; then,
+// in the same kernel, each n still open probes the primes KA+1 .. K in order
+// (KA = 64 x blocks).  Needs K >= KA, H = 4 (mod 64) and no p_min array.
 int cover_fast_phase_primes(uint32_t K, uint64_t n_hi);   // KA for K primes near n_hi (0: none)
 cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s);
 

@@ -199,12 +199,18 @@ def test_two_phase_without_retry_counts_unresolved(gbm, oracle):
     assert r["max_pmin"] == int(ref.max())
 
 
-def test_two_phase_matches_generic(gbm, monkeypatch):
-    """The two-phase and the generic cover kernels give identical results."""
-    lo, hi = 3 * 10**11, 3 * 10**11 + 2 * 5 * 10**6
+@pytest.mark.parametrize("ka", ["64", "128", "192", "256"])
+@pytest.mark.parametrize("lo", [10**6, 3 * 10**11])
+def test_two_phase_matches_generic(gbm, monkeypatch, ka, lo):
+    """The block cover (1 to 4 unrolled blocks of 64 primes, so the segment
+    maximum comes from the probing or from a re-run of the last block) and the
+    generic cover kernel give identical results."""
+    hi = lo + 2 * 5 * 10**6
     base = dict(device=0, base_limit=1 << 20, seg_len=1 << 20, p1=1 << 15, p2=1 << 20)
+    monkeypatch.setenv("GB_KA", ka)
     with gbm.Context(**base) as g:
         a = g.verify_range(lo, hi, seg_hist_stride=3512, hist_cap=3512)
+    monkeypatch.delenv("GB_KA")
     monkeypatch.setenv("GB_COVER", "generic")
     with gbm.Context(**base) as g:
         b = g.verify_range(lo, hi, seg_hist_stride=3512, hist_cap=3512)
