@@ -51,10 +51,10 @@ __host__ __device__ constexpr uint32_t odd_prime(int k)
 }
 
 // cumulative counts are kept three per register (10-bit fields): a lane adds
-// at most 32 per word and handles at most 31 words per CTA (32 * 31 < 2^10)
+// at most 32 per word and handles at most 31 words per CTA in a block
+// (32 * 31 < 2^10)
 constexpr int kCumBits = 10;
 constexpr uint32_t kCumMask = (1u << kCumBits) - 1;
-constexpr int kMaxWordsPerLane = 31;
 __host__ __device__ constexpr int cum_regs(int KA) { return (KA + 2) / 3; }
 
 // ---------------------------------------------------------------------------
@@ -111,11 +111,54 @@ __device__ __forceinline__ void flush_block(const uint32_t (&cum)[KH], uint32_t 
     }
 }
 
+// ---------------------------------------------------------------------------
+// block 0 on three consecutive words per lane.  The histogram needs, per step,
+// popc(C0) + popc(C1) + popc(C2); a carry-save adder gives it with two
+// popcounts: ones = C0 ^ C1 ^ C2, twos = majority(C0, C1, C2), and
+// popc(C0) + popc(C1) + popc(C2) = popc(ones) + 2 popc(twos).
+// Window: R[t] = Q32[w + 2 + d_3/32 - t] for the lane's first word w.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int block0_regs3() { return (int)((step_e(kBlock - 1) + 31) / 32) + 3; }
+
+template <int K, int NR3, int KH>
+__device__ __forceinline__ void step3(const uint32_t (&R)[NR3], uint32_t& C0, uint32_t& C1, uint32_t& C2,
+                                      uint32_t (&cum)[KH])
+{
+    constexpr uint32_t e = step_e(K);
+    constexpr int c = (int)((e + 31) / 32);
+    constexpr uint32_t sh = 32 * c - e;
+    static_assert(c + 2 < NR3, "window too small");
+    uint32_t s0, s1, s2;
+    if constexpr (sh == 0) {
+        s0 = R[c + 2]; s1 = R[c + 1]; s2 = R[c];
+    } else {
+        s0 = __funnelshift_r(R[c + 2], R[c + 1], sh);
+        s1 = __funnelshift_r(R[c + 1], R[c], sh);
+        s2 = __funnelshift_r(R[c], R[c - 1], sh);
+    }
+    C0 |= s0;
+    C1 |= s1;
+    C2 |= s2;
+    const uint32_t ones = C0 ^ C1 ^ C2;
+    const uint32_t twos = (C0 & C1) | (C0 & C2) | (C1 & C2);
+    const uint32_t t = __popc(ones) + 2 * __popc(twos);
+    if constexpr (K % 3 == 0) cum[K / 3] += t;
+    else cum[K / 3] += t << (kCumBits * (K % 3));
+}
+
+template <int NR3, int KH, int... J>
+__device__ __forceinline__ void run_block0_3(std::integer_sequence<int, J...>, const uint32_t (&R)[NR3], uint32_t& C0,
+                                             uint32_t& C1, uint32_t& C2, uint32_t (&cum)[KH])
+{
+    (step3<J, NR3, KH>(R, C0, C1, C2, cum), ...);
+}
+
+
 // Block b > 0 over the compacted words of list `in` (n_in entries); words
 // still open are appended to `out`.  Entries: word (CTA-relative) and C.
 template <int NT, int K0>
-__device__ __forceinline__ void later_block(const uint32_t* Qc, uint32_t D0w, const uint32_t* in_w,
-                                            const uint32_t* in_c, uint32_t n_in, uint32_t* out_w, uint32_t* out_c,
+__device__ __forceinline__ void later_block(const uint32_t* Qc, uint32_t D0w, const uint16_t* in_w,
+                                            const uint32_t* in_c, uint32_t n_in, uint16_t* out_w, uint32_t* out_c,
                                             uint32_t* n_out, uint32_t* shist, uint32_t& nsteps)
 {
     constexpr int NR = block_regs(K0);
@@ -145,7 +188,7 @@ __device__ __forceinline__ void later_block(const uint32_t* Qc, uint32_t D0w, co
         run_block<K0, NR, KH>(std::make_integer_sequence<int, kBlock>{}, R, C, cum);
         if (C != 0xffffffffu) {
             const uint32_t slot = atomicAdd(n_out, 1u);
-            out_w[slot] = wrel;
+            out_w[slot] = (uint16_t)wrel;
             out_c[slot] = C;
         }
     }
@@ -178,7 +221,7 @@ __device__ __forceinline__ void track_block_steps(std::integer_sequence<int, J..
 }
 
 template <int NT, int K0>
-__device__ __forceinline__ unsigned long long track_block(const uint32_t* Qc, uint32_t D0w, const uint32_t* in_w,
+__device__ __forceinline__ unsigned long long track_block(const uint32_t* Qc, uint32_t D0w, const uint16_t* in_w,
                                                           const uint32_t* in_c, uint32_t n_in, uint32_t j_cta)
 {
     constexpr int NR = block_regs(K0);
@@ -208,8 +251,8 @@ __device__ __forceinline__ unsigned long long track_block(const uint32_t* Qc, ui
 // Phase B over a list of open words: the warp takes the open n one at a time,
 // lane t probing the prime k + t; the lowest set bit of the ballot is p_min.
 template <int NT>
-__device__ __forceinline__ void probe_open(const CoverArgs& a, const uint32_t* Qc, const uint32_t* sd,
-                                           const uint32_t* in_w, const uint32_t* in_c, uint32_t n_in,
+__device__ __forceinline__ void probe_open(const CoverArgs& a, const uint32_t* Qc,
+                                           const uint16_t* in_w, const uint32_t* in_c, uint32_t n_in,
                                            uint32_t k_first, uint64_t w_begin, uint32_t j_cta, uint32_t seg,
                                            uint32_t* shist, unsigned long long& best, uint32_t& nsteps)
 {
@@ -227,7 +270,7 @@ __device__ __forceinline__ void probe_open(const CoverArgs& a, const uint32_t* Q
                 const uint32_t kt = k + (uint32_t)lane;
                 uint32_t bit = 0;
                 if (kt < a.K) {
-                    const uint32_t i = rel + sd[kt];
+                    const uint32_t i = rel + ((a.H - __ldg(a.primes + 1 + kt) - 1) >> 1);
                     bit = (__ldg(Qc + (i >> 5)) >> (i & 31)) & 1u;
                 }
                 const unsigned hb = __ballot_sync(0xffffffffu, bit);
@@ -274,9 +317,8 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     constexpr int NR = block_regs(0);
     constexpr int KH = (kBlock + 2) / 3;
     extern __shared__ uint32_t smem[];
-    uint32_t* sd = smem;                                    // d_k for the K odd primes
-    uint32_t* shist = sd + a.K;                             // K + 1 counters
-    uint32_t* lists = shist + a.K + 1;                      // 2 lists x (words, C), cta words each
+    uint32_t* shist = smem;                                 // K + 1 counters
+    uint32_t* lists = smem + ((a.K + 1 + 3) & ~3u);         // 2 lists: C (32-bit), then words (16-bit)
     __shared__ unsigned long long smax;
     __shared__ uint32_t counts[2];
 
@@ -293,11 +335,10 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
     if (w_end > n_words32) w_end = n_words32;
     const uint32_t cap = 2 * a.cta_words;                   // list capacity: every word of the CTA
-    // list i: words at lists + 2*cap*i, coverage right after them
-    auto lw = [&](int i) { return lists + 2 * cap * (uint32_t)i; };
-    auto lc = [&](int i) { return lists + 2 * cap * (uint32_t)i + cap; };
+    // list i: coverage at lists + cap*i, word indices (16-bit) after both
+    auto lc = [&](int i) { return lists + cap * (uint32_t)i; };
+    auto lw = [&](int i) { return reinterpret_cast<uint16_t*>(lists + 2 * cap) + cap * (uint32_t)i; };
 
-    for (uint32_t k = threadIdx.x; k < a.K; k += NT) sd[k] = (a.H - a.primes[1 + k] - 1) >> 1;
     for (uint32_t k = threadIdx.x; k <= a.K; k += NT) shist[k] = 0;
     if (threadIdx.x == 0) { smax = 0; counts[0] = 0; counts[1] = 0; }
     __syncthreads();
@@ -310,38 +351,54 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     const uint32_t j_cta = (uint32_t)(32 * (w_begin - seg_w0));   // segment-relative n of the CTA's first n
 
     uint32_t nsteps = 0;
-    // block 0 over every word
+    // block 0 over every word, three consecutive words per lane
     {
+        constexpr int NR3 = block0_regs3();
+        constexpr int KH = (kBlock + 2) / 3;
         uint32_t cum[KH];
 #pragma unroll
         for (int k = 0; k < KH; ++k) cum[k] = 0;
         uint32_t init_pop = 0;
-        for (uint32_t wbase = 32 * warp; wbase < nw_cta; wbase += 32 * NW) {
-            const uint32_t wrel = wbase + lane;
-            const bool active = wrel < nw_cta;
-            uint32_t C = 0xffffffffu;
-            uint32_t R[NR];
-            if (active) {
-                C = 0;
-                const uint32_t j0 = 32 * wrel;
-                if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);   // past the slab end
-                if (a.has_n4 && w_begin + wrel == 0) {
-                    C |= 1u;                                     // n = 4 = 2 + 2
-                    atomicAdd(&shist[0], 1u);
-                }
+        for (uint32_t wbase = 96 * warp; wbase < nw_cta; wbase += 96 * NW) {
+            const uint32_t wl = wbase + 3 * (uint32_t)lane;           // the lane's first word
+            uint32_t Cw[3];
 #pragma unroll
-                for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - t);
+            for (int i = 0; i < 3; ++i) {
+                const uint32_t w = wl + i;
+                uint32_t C = 0xffffffffu;
+                if (w < nw_cta) {
+                    C = 0;
+                    const uint32_t j0 = 32 * w;
+                    if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);   // past the slab end
+                    if (a.has_n4 && w_begin + w == 0) {
+                        C |= 1u;                                         // n = 4 = 2 + 2
+                        atomicAdd(&shist[0], 1u);
+                    }
+                    nsteps += kBlock;
+                }
+                Cw[i] = C;
+                init_pop += __popc(C);
+            }
+            uint32_t R[NR3];
+            if (wl < nw_cta) {
+                // the top word read, wl + 2, lies at most one word past the CTA's
+                // last word: inside the q window, which runs past the slab
+#pragma unroll
+                for (int t = 0; t < NR3; ++t) R[t] = __ldg(Qc + wl + 2 + D0w - t);
             } else {
 #pragma unroll
-                for (int t = 0; t < NR; ++t) R[t] = 0;
+                for (int t = 0; t < NR3; ++t) R[t] = 0;
             }
-            init_pop += __popc(C);
-            nsteps += active ? kBlock : 0;
-            run_block<0, NR, KH>(std::make_integer_sequence<int, kBlock>{}, R, C, cum);
-            if (C != 0xffffffffu) {
-                const uint32_t slot = atomicAdd(&counts[0], 1u);
-                lw(0)[slot] = wrel;
-                lc(0)[slot] = C;
+            uint32_t C0 = Cw[0], C1 = Cw[1], C2 = Cw[2];
+            run_block0_3<NR3, KH>(std::make_integer_sequence<int, kBlock>{}, R, C0, C1, C2, cum);
+            Cw[0] = C0; Cw[1] = C1; Cw[2] = C2;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (Cw[i] != 0xffffffffu) {
+                    const uint32_t slot = atomicAdd(&counts[0], 1u);
+                    lw(0)[slot] = (uint16_t)(wl + i);
+                    lc(0)[slot] = Cw[i];
+                }
             }
         }
         flush_block<0, KH>(cum, init_pop, shist, lane);
@@ -374,7 +431,7 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     if constexpr (NB >= 4) run_later(std::integral_constant<int, 192>{});
 
     unsigned long long best = 0;                            // lane 0 of each warp
-    probe_open<NT>(a, Qc, sd, lw(cur), lc(cur), n_cur, (uint32_t)(kBlock * NB), w_begin, j_cta, seg, shist,
+    probe_open<NT>(a, Qc, lw(cur), lc(cur), n_cur, (uint32_t)(kBlock * NB), w_begin, j_cta, seg, shist,
                    best, nsteps);
     if (lane == 0 && best) atomicMax(&smax, best);
     __syncthreads();
@@ -389,7 +446,7 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
                 const uint32_t j0 = 32 * w;
                 if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);
                 if (a.has_n4 && w_begin + w == 0) C |= 1u;
-                lw(1)[w] = w;
+                lw(1)[w] = (uint16_t)w;
                 lc(1)[w] = C;
             }
             __syncthreads();
@@ -441,7 +498,8 @@ static cudaError_t launch_nb(const CoverArgs& a, cudaStream_t s)
     constexpr int NT = 256;
     const unsigned grid = a.nseg * a.chunks_per_seg;
     if (grid == 0) return cudaSuccess;
-    const size_t smem = (size_t)(2 * a.K + 1 + 8 * a.cta_words) * 4;
+    // histogram, then two lists of the CTA's words: 32-bit coverage, 16-bit index
+    const size_t smem = (size_t)((a.K + 1 + 3) & ~3u) * 4 + (size_t)2 * (2 * a.cta_words) * 6;
     auto k = k_cover_fast<NT, NB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -451,9 +509,10 @@ static cudaError_t launch_nb(const CoverArgs& a, cudaStream_t s)
 
 cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s)
 {
-    // 10-bit counters hold a lane's sum of at most 32 per word over its words
-    // of a CTA
-    if (2ull * a.cta_words > (unsigned long long)kMaxWordsPerLane * 256) return cudaErrorInvalidValue;
+    // 10-bit counters: in block 0 a lane adds at most 96 per step per round
+    // (three words), at most 10 rounds of 768 words; later blocks add at most
+    // 32 per listed word, at most 30 per lane
+    if (2ull * a.cta_words > 10ull * 768) return cudaErrorInvalidValue;
     switch (KA) {
     case 64: return launch_nb<1>(a, s);
     case 128: return launch_nb<2>(a, s);
