@@ -57,6 +57,20 @@ constexpr int kCumBits = 10;
 constexpr uint32_t kCumMask = (1u << kCumBits) - 1;
 __host__ __device__ constexpr int cum_regs(int KA) { return (KA + 2) / 3; }
 
+// reserve one list slot per lane with `want` set: one shared atomic per warp,
+// each lane's slot = base + its rank among the lanes that want one
+__device__ __forceinline__ uint32_t warp_slot(bool want, uint32_t* counter, int lane)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    uint32_t base = 0;
+    if (m) {
+        const int leader = __ffs(m) - 1;
+        if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+    }
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+
 // ---------------------------------------------------------------------------
 // one unrolled block of 64 primes: indices K0 .. K0+63, window registers
 // R[t] = Q32[base - C0 - t] with C0 = the first block step's word offset - 1
@@ -186,8 +200,9 @@ __device__ __forceinline__ void later_block(const uint32_t* Qc, uint32_t D0w, co
         init_pop += __popc(C);
         nsteps += active ? kBlock : 0;
         run_block<K0, NR, KH>(std::make_integer_sequence<int, kBlock>{}, R, C, cum);
-        if (C != 0xffffffffu) {
-            const uint32_t slot = atomicAdd(n_out, 1u);
+        const bool open = C != 0xffffffffu;
+        const uint32_t slot = warp_slot(open, n_out, lane);
+        if (open) {
             out_w[slot] = (uint16_t)wrel;
             out_c[slot] = C;
         }
@@ -394,8 +409,9 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
             Cw[0] = C0; Cw[1] = C1; Cw[2] = C2;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                if (Cw[i] != 0xffffffffu) {
-                    const uint32_t slot = atomicAdd(&counts[0], 1u);
+                const bool open = Cw[i] != 0xffffffffu;
+                const uint32_t slot = warp_slot(open, &counts[0], lane);
+                if (open) {
                     lw(0)[slot] = (uint16_t)(wl + i);
                     lc(0)[slot] = Cw[i];
                 }
