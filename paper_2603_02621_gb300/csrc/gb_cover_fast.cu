@@ -269,7 +269,7 @@ template <int NT>
 __device__ __forceinline__ void probe_open(const CoverArgs& a, const uint32_t* Qc,
                                            const uint16_t* in_w, const uint32_t* in_c, uint32_t n_in,
                                            uint32_t k_first, uint64_t w_begin, uint32_t j_cta, uint32_t seg,
-                                           uint32_t* shist, unsigned long long& best, uint32_t& nsteps)
+                                           unsigned long long& best, uint32_t& nsteps)
 {
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -293,7 +293,7 @@ __device__ __forceinline__ void probe_open(const CoverArgs& a, const uint32_t* Q
                 if (hb) {
                     const uint32_t kk = k + (__ffs(hb) - 1);
                     if (lane == 0) {
-                        atomicAdd(&shist[kk + 1], 1u);
+                        atomicAdd(&a.hist[(uint64_t)seg * a.hist_stride + kk + 1], 1u);
                         const unsigned long long key =
                             ((unsigned long long)(kk + 2) << 32) | (0xffffffffull - (j_cta + rel));
                         if (key > best) best = key;
@@ -331,9 +331,8 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     constexpr int NW = NT / 32;
     constexpr int NR = block_regs(0);
     constexpr int KH = (kBlock + 2) / 3;
-    extern __shared__ uint32_t smem[];
-    uint32_t* shist = smem;                                 // K + 1 counters
-    uint32_t* lists = smem + ((a.K + 1 + 3) & ~3u);         // 2 lists: C (32-bit), then words (16-bit)
+    extern __shared__ uint32_t lists[];                     // 2 lists: C (32-bit), then words (16-bit)
+    __shared__ uint32_t shist[kBlock * NB + 1];             // bins of the unrolled blocks' primes
     __shared__ unsigned long long smax;
     __shared__ uint32_t counts[2];
 
@@ -354,7 +353,7 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     auto lc = [&](int i) { return lists + cap * (uint32_t)i; };
     auto lw = [&](int i) { return reinterpret_cast<uint16_t*>(lists + 2 * cap) + cap * (uint32_t)i; };
 
-    for (uint32_t k = threadIdx.x; k <= a.K; k += NT) shist[k] = 0;
+    for (uint32_t k = threadIdx.x; k <= (uint32_t)(kBlock * NB); k += NT) shist[k] = 0;
     if (threadIdx.x == 0) { smax = 0; counts[0] = 0; counts[1] = 0; }
     __syncthreads();
 
@@ -447,8 +446,7 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     if constexpr (NB >= 4) run_later(std::integral_constant<int, 192>{});
 
     unsigned long long best = 0;                            // lane 0 of each warp
-    probe_open<NT>(a, Qc, lw(cur), lc(cur), n_cur, (uint32_t)(kBlock * NB), w_begin, j_cta, seg, shist,
-                   best, nsteps);
+    probe_open<NT>(a, Qc, lw(cur), lc(cur), n_cur, (uint32_t)(kBlock * NB), w_begin, j_cta, seg, best, nsteps);
     if (lane == 0 && best) atomicMax(&smax, best);
     __syncthreads();
     if (smax == 0) {
@@ -494,7 +492,7 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
         if (lane == 0 && t) atomicAdd(a.iters, t);
     }
     uint32_t* hrow = a.hist + (uint64_t)seg * a.hist_stride;
-    for (uint32_t kk = threadIdx.x; kk <= a.K; kk += NT)
+    for (uint32_t kk = threadIdx.x; kk <= (uint32_t)(kBlock * NB); kk += NT)
         if (shist[kk]) atomicAdd(&hrow[kk], shist[kk]);
     if (threadIdx.x == 0 && smax) atomicMax(&a.maxkey[seg], smax);
 }
@@ -514,8 +512,8 @@ static cudaError_t launch_nb(const CoverArgs& a, cudaStream_t s)
     constexpr int NT = 256;
     const unsigned grid = a.nseg * a.chunks_per_seg;
     if (grid == 0) return cudaSuccess;
-    // histogram, then two lists of the CTA's words: 32-bit coverage, 16-bit index
-    const size_t smem = (size_t)((a.K + 1 + 3) & ~3u) * 4 + (size_t)2 * (2 * a.cta_words) * 6;
+    // two lists of the CTA's words: 32-bit coverage, 16-bit index
+    const size_t smem = (size_t)2 * (2 * a.cta_words) * 6;
     auto k = k_cover_fast<NT, NB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
