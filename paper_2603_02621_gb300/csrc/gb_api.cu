@@ -545,8 +545,9 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
         if (KA && ctx->ka_override && (uint32_t)ctx->ka_override <= K1) KA = ctx->ka_override;
         if (KA) {
-            // the block cover keeps two lists of the CTA's words in shared memory
-            ca.cta_words = std::min<uint32_t>(2048, (uint32_t)(S / 64));
+            // block cover: 7680 32-bit words per CTA (ten rounds of 96 words per
+            // warp, the most its 10-bit counters allow)
+            ca.cta_words = std::min<uint32_t>(3840, (uint32_t)(S / 64));
             ca.chunks_per_seg = (uint32_t)((S / 64 + ca.cta_words - 1) / ca.cta_words);
         }
         ctx->prof_begin(kProfCover, n_count);

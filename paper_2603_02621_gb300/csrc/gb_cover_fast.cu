@@ -57,20 +57,6 @@ constexpr int kCumBits = 10;
 constexpr uint32_t kCumMask = (1u << kCumBits) - 1;
 __host__ __device__ constexpr int cum_regs(int KA) { return (KA + 2) / 3; }
 
-// reserve one list slot per lane with `want` set: one shared atomic per warp,
-// each lane's slot = base + its rank among the lanes that want one
-__device__ __forceinline__ uint32_t warp_slot(bool want, uint32_t* counter, int lane)
-{
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    uint32_t base = 0;
-    if (m) {
-        const int leader = __ffs(m) - 1;
-        if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-    }
-    return base + __popc(m & ((1u << lane) - 1u));
-}
-
 // ---------------------------------------------------------------------------
 // one unrolled block of 64 primes: indices K0 .. K0+63, window registers
 // R[t] = Q32[base - C0 - t] with C0 = the first block step's word offset - 1
@@ -168,48 +154,6 @@ __device__ __forceinline__ void run_block0_3(std::integer_sequence<int, J...>, c
 }
 
 
-// Block b > 0 over the compacted words of list `in` (n_in entries); words
-// still open are appended to `out`.  Entries: word (CTA-relative) and C.
-template <int NT, int K0>
-__device__ __forceinline__ void later_block(const uint32_t* Qc, uint32_t D0w, const uint16_t* in_w,
-                                            const uint32_t* in_c, uint32_t n_in, uint16_t* out_w, uint32_t* out_c,
-                                            uint32_t* n_out, uint32_t* shist, uint32_t& nsteps)
-{
-    constexpr int NR = block_regs(K0);
-    constexpr int KH = (kBlock + 2) / 3;
-    constexpr int C0 = block_c0(K0);
-    const int lane = threadIdx.x & 31;
-    uint32_t cum[KH];
-#pragma unroll
-    for (int j = 0; j < KH; ++j) cum[j] = 0;
-    uint32_t init_pop = 0;
-    for (uint32_t b = threadIdx.x - lane; b < n_in; b += NT) {
-        const uint32_t e = b + lane;
-        const bool active = e < n_in;
-        uint32_t C = 0xffffffffu, wrel = 0;
-        uint32_t R[NR];
-        if (active) {
-            wrel = in_w[e];
-            C = in_c[e];
-#pragma unroll
-            for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - C0 - t);
-        } else {
-#pragma unroll
-            for (int t = 0; t < NR; ++t) R[t] = 0;
-        }
-        init_pop += __popc(C);
-        nsteps += active ? kBlock : 0;
-        run_block<K0, NR, KH>(std::make_integer_sequence<int, kBlock>{}, R, C, cum);
-        const bool open = C != 0xffffffffu;
-        const uint32_t slot = warp_slot(open, n_out, lane);
-        if (open) {
-            out_w[slot] = (uint16_t)wrel;
-            out_c[slot] = C;
-        }
-    }
-    flush_block<K0, KH>(cum, init_pop, shist, lane);
-}
-
 // Re-run block K0 over its input list recording, per word, the last step that
 // set a bit and the lowest bit it set: the largest p_min among the list's
 // words, with its smallest n.  Used when no n of the CTA outlived the blocks.
@@ -235,47 +179,118 @@ __device__ __forceinline__ void track_block_steps(std::integer_sequence<int, J..
     (track_step<K0 + J, K0, NR>(R, C, last, lastbits), ...);
 }
 
-template <int NT, int K0>
-__device__ __forceinline__ unsigned long long track_block(const uint32_t* Qc, uint32_t D0w, const uint16_t* in_w,
-                                                          const uint32_t* in_c, uint32_t n_in, uint32_t j_cta)
+// step of a tracked block: also records the last step that set a bit and the
+// bits it set
+template <int K, int K0, int NR, int KH>
+__device__ __forceinline__ void block_step_tracked(const uint32_t (&R)[NR], uint32_t& C, uint32_t (&cum)[KH],
+                                                   uint32_t& last, uint32_t& lastbits)
+{
+    constexpr uint32_t e = step_e(K);
+    constexpr int c = (int)((e + 31) / 32);
+    constexpr uint32_t sh = 32 * c - e;
+    constexpr int r = c - block_c0(K0);
+    static_assert(r >= 0 && r < NR, "window too small");
+    uint32_t s;
+    if constexpr (sh == 0) s = R[r];
+    else s = __funnelshift_r(R[r], R[r - 1], sh);
+    const uint32_t nw = s & ~C;
+    C |= s;
+    if (nw) { last = K + 1; lastbits = nw; }
+    constexpr int j = K - K0;
+    if constexpr (j % 3 == 0) cum[j / 3] += __popc(C);
+    else cum[j / 3] += __popc(C) << (kCumBits * (j % 3));
+}
+
+template <int K0, int NR, int KH, int... J>
+__device__ __forceinline__ void run_block_tracked(std::integer_sequence<int, J...>, const uint32_t (&R)[NR],
+                                                  uint32_t& C, uint32_t (&cum)[KH], uint32_t& last,
+                                                  uint32_t& lastbits)
+{
+    (block_step_tracked<K0 + J, K0, NR, KH>(R, C, cum, last, lastbits), ...);
+}
+
+// block K0 on one word with tracking only (no histogram): the key of its
+// largest p_min with the smallest n, 0 if the block set no bit
+template <int K0>
+__device__ __forceinline__ unsigned long long track_word(const uint32_t* Qc, uint32_t D0w, uint32_t wrel, uint32_t C,
+                                                         uint32_t j_cta)
 {
     constexpr int NR = block_regs(K0);
     constexpr int C0 = block_c0(K0);
-    const int lane = threadIdx.x & 31;
-    unsigned long long best = 0;
-    for (uint32_t b = threadIdx.x - lane; b < n_in; b += NT) {
-        const uint32_t e = b + lane;
-        if (e >= n_in) break;
-        const uint32_t wrel = in_w[e];
-        uint32_t C = in_c[e];
-        uint32_t R[NR];
+    uint32_t R[NR];
 #pragma unroll
-        for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - C0 - t);
+    for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - C0 - t);
+    uint32_t last = 0, lastbits = 0;
+    track_block_steps<K0, NR>(std::make_integer_sequence<int, kBlock>{}, R, C, last, lastbits);
+    if (!last) return 0;
+    const uint32_t j = j_cta + 32 * wrel + (__ffs(lastbits) - 1);
+    return ((unsigned long long)(last + 1) << 32) | (0xffffffffull - j);
+}
+
+// Later block K0 over a warp's list, batches of 32 words (one per lane),
+// with per-word tracking of the last step that set a bit; words still open
+// are compacted in place at the front of the list (writes never pass reads).
+template <int K0>
+__device__ __forceinline__ uint32_t later_block_warp(const uint32_t* Qc, uint32_t D0w, uint16_t* lw, uint32_t* lc,
+                                                     uint32_t n_in, uint32_t* shist, uint32_t j_cta,
+                                                     unsigned long long& best, uint32_t& nsteps)
+{
+    constexpr int NR = block_regs(K0);
+    constexpr int KH = (kBlock + 2) / 3;
+    constexpr int C0 = block_c0(K0);
+    const int lane = threadIdx.x & 31;
+    uint32_t cum[KH];
+#pragma unroll
+    for (int j = 0; j < KH; ++j) cum[j] = 0;
+    uint32_t init_pop = 0, n_out = 0;
+    for (uint32_t b = 0; b < n_in; b += 32) {
+        const uint32_t e = b + lane;
+        const bool active = e < n_in;
+        uint32_t C = 0xffffffffu, wrel = 0;
+        uint32_t R[NR];
+        if (active) {
+            wrel = lw[e];
+            C = lc[e];
+#pragma unroll
+            for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - C0 - t);
+        } else {
+#pragma unroll
+            for (int t = 0; t < NR; ++t) R[t] = 0;
+        }
+        __syncwarp();                                      // the batch is read before outputs land
+        init_pop += __popc(C);
+        nsteps += active ? kBlock : 0;
         uint32_t last = 0, lastbits = 0;
-        track_block_steps<K0, NR>(std::make_integer_sequence<int, kBlock>{}, R, C, last, lastbits);
+        run_block_tracked<K0, NR, KH>(std::make_integer_sequence<int, kBlock>{}, R, C, cum, last, lastbits);
         if (last) {
-            // prime index of step K is K + 1 (index 0 is the prime 2): key holds index + 1
             const uint32_t j = j_cta + 32 * wrel + (__ffs(lastbits) - 1);
             const unsigned long long key = ((unsigned long long)(last + 1) << 32) | (0xffffffffull - j);
             if (key > best) best = key;
         }
+        const bool open = C != 0xffffffffu;
+        const unsigned m = __ballot_sync(0xffffffffu, open);
+        if (open) {
+            const uint32_t slot = n_out + __popc(m & ((1u << lane) - 1u));
+            lw[slot] = (uint16_t)wrel;
+            lc[slot] = C;
+        }
+        n_out += __popc(m);
+        __syncwarp();
     }
-    return best;
+    flush_block<K0, KH>(cum, init_pop, shist, lane);
+    return n_out;
 }
 
-// Phase B over a list of open words: the warp takes the open n one at a time,
-// lane t probing the prime k + t; the lowest set bit of the ballot is p_min.
-template <int NT>
-__device__ __forceinline__ void probe_open(const CoverArgs& a, const uint32_t* Qc,
-                                           const uint16_t* in_w, const uint32_t* in_c, uint32_t n_in,
-                                           uint32_t k_first, uint64_t w_begin, uint32_t j_cta, uint32_t seg,
-                                           unsigned long long& best, uint32_t& nsteps)
+// Probing over a warp's list: the warp takes the open n one at a time, lane t
+// probing the prime k + t; the lowest set bit of the ballot is p_min.
+__device__ __forceinline__ void probe_warp(const CoverArgs& a, const uint32_t* Qc, const uint16_t* lw,
+                                           const uint32_t* lc, uint32_t n_in, uint32_t k_first, uint64_t w_begin,
+                                           uint32_t j_cta, uint32_t seg, unsigned long long& best, uint32_t& nsteps)
 {
-    constexpr int NW = NT / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t e = warp; e < n_in; e += NW) {
-        const uint32_t wrel = in_w[e];
-        uint32_t mm = ~in_c[e];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = 0; e < n_in; ++e) {
+        const uint32_t wrel = lw[e];
+        uint32_t mm = ~lc[e];
         while (mm) {
             const uint32_t b = __ffs(mm) - 1;
             mm &= mm - 1;
@@ -323,18 +338,15 @@ __device__ __forceinline__ void probe_open(const CoverArgs& a, const uint32_t* Q
     }
 }
 
-// NB unrolled blocks of 64 primes (the first over every word, the later ones
-// over the words still open), then per-n probing
+// NB unrolled blocks of 64 primes (block 0 over every word, three words per
+// lane; later blocks over the words still open, per warp), then per-n probing.
 template <int NT, int NB>
 __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
 {
     constexpr int NW = NT / 32;
-    constexpr int NR = block_regs(0);
-    constexpr int KH = (kBlock + 2) / 3;
-    extern __shared__ uint32_t lists[];                     // 2 lists: C (32-bit), then words (16-bit)
+    extern __shared__ uint32_t smem[];                      // per warp: list C (32-bit), then words (16-bit)
     __shared__ uint32_t shist[kBlock * NB + 1];             // bins of the unrolled blocks' primes
     __shared__ unsigned long long smax;
-    __shared__ uint32_t counts[2];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -348,13 +360,13 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     const uint64_t n_words32 = (a.n_count + 31) / 32;
     if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
     if (w_end > n_words32) w_end = n_words32;
-    const uint32_t cap = 2 * a.cta_words;                   // list capacity: every word of the CTA
-    // list i: coverage at lists + cap*i, word indices (16-bit) after both
-    auto lc = [&](int i) { return lists + cap * (uint32_t)i; };
-    auto lw = [&](int i) { return reinterpret_cast<uint16_t*>(lists + 2 * cap) + cap * (uint32_t)i; };
+    // a warp's list holds every word it takes in block 0
+    const uint32_t cap = (2 * a.cta_words + 96 * NW - 1) / (96 * NW) * 96;
+    uint32_t* lc = smem + (uint32_t)warp * cap;
+    uint16_t* lw = reinterpret_cast<uint16_t*>(smem + NW * cap) + (uint32_t)warp * cap;
 
     for (uint32_t k = threadIdx.x; k <= (uint32_t)(kBlock * NB); k += NT) shist[k] = 0;
-    if (threadIdx.x == 0) { smax = 0; counts[0] = 0; counts[1] = 0; }
+    if (threadIdx.x == 0) smax = 0;
     __syncthreads();
 
     const uint32_t* Qc = reinterpret_cast<const uint32_t*>(a.Q) + w_begin;   // CTA-relative words
@@ -364,8 +376,8 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     const uint32_t n_rel_end = (uint32_t)(n_left < 32ull * nw_cta ? n_left : 32ull * nw_cta);
     const uint32_t j_cta = (uint32_t)(32 * (w_begin - seg_w0));   // segment-relative n of the CTA's first n
 
-    uint32_t nsteps = 0;
-    // block 0 over every word, three consecutive words per lane
+    uint32_t nsteps = 0, n_open = 0;
+    // block 0 over every word of this warp, three consecutive words per lane
     {
         constexpr int NR3 = block0_regs3();
         constexpr int KH = (kBlock + 2) / 3;
@@ -409,73 +421,49 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const bool open = Cw[i] != 0xffffffffu;
-                const uint32_t slot = warp_slot(open, &counts[0], lane);
+                const unsigned m = __ballot_sync(0xffffffffu, open);
                 if (open) {
-                    lw(0)[slot] = (uint16_t)(wl + i);
-                    lc(0)[slot] = Cw[i];
+                    const uint32_t slot = n_open + __popc(m & ((1u << lane) - 1u));
+                    lw[slot] = (uint16_t)(wl + i);
+                    lc[slot] = Cw[i];
                 }
+                n_open += __popc(m);
             }
         }
         flush_block<0, KH>(cum, init_pop, shist, lane);
     }
-    __syncthreads();
-    // later blocks over the words still open.  The lists alternate: a block
-    // reads one and writes the other, and a block with no input writes
-    // nothing, so the input list of the last block that ran stays intact.
-    int cur = 0;                      // list holding the words still open
-    uint32_t n_cur = counts[0];
-    int last_in = 0;                  // last block that ran (0: block 0, input = every word)
-    int last_list = 0;                // its input list (later blocks)
-    uint32_t last_n = 0;              // and that list's length
-    auto run_later = [&](auto k0_tag) {
-        constexpr int K0 = decltype(k0_tag)::value;
-        if (n_cur == 0) return;
-        const int out = cur ^ 1;
-        if (threadIdx.x == 0) counts[out] = 0;
-        __syncthreads();
-        later_block<NT, K0>(Qc, D0w, lw(cur), lc(cur), n_cur, lw(out), lc(out), &counts[out], shist, nsteps);
-        __syncthreads();
-        last_in = K0 / kBlock;
-        last_list = cur;
-        last_n = n_cur;
-        cur = out;
-        n_cur = counts[out];
-    };
-    if constexpr (NB >= 2) run_later(std::integral_constant<int, 64>{});
-    if constexpr (NB >= 3) run_later(std::integral_constant<int, 128>{});
-    if constexpr (NB >= 4) run_later(std::integral_constant<int, 192>{});
+    __syncwarp();
+    unsigned long long best = 0;
+    if constexpr (NB >= 2) n_open = later_block_warp<64>(Qc, D0w, lw, lc, n_open, shist, j_cta, best, nsteps);
+    if constexpr (NB >= 3) n_open = later_block_warp<128>(Qc, D0w, lw, lc, n_open, shist, j_cta, best, nsteps);
+    if constexpr (NB >= 4) n_open = later_block_warp<192>(Qc, D0w, lw, lc, n_open, shist, j_cta, best, nsteps);
+    probe_warp(a, Qc, lw, lc, n_open, (uint32_t)(kBlock * NB), w_begin, j_cta, seg, best, nsteps);
 
-    unsigned long long best = 0;                            // lane 0 of each warp
-    probe_open<NT>(a, Qc, lw(cur), lc(cur), n_cur, (uint32_t)(kBlock * NB), w_begin, j_cta, seg, best, nsteps);
-    if (lane == 0 && best) atomicMax(&smax, best);
+    // maximum: warp, CTA
+    {
+        const uint32_t khi = (uint32_t)(best >> 32);
+        const uint32_t mhi = __reduce_max_sync(0xffffffffu, khi);
+        const uint32_t klo = khi == mhi ? (uint32_t)best : 0u;
+        const uint32_t mlo = __reduce_max_sync(0xffffffffu, klo);
+        if (lane == 0 && mhi) atomicMax(&smax, ((unsigned long long)mhi << 32) | mlo);
+    }
     __syncthreads();
     if (smax == 0) {
-        // no n outlived the blocks with a prime found: the maximum is in the
-        // last block that ran, among that block's input words
-        if (last_in == 0) {
-            // block 0's input is every word of the CTA: rebuild it (both lists
-            // are free: block 0 left no open word)
-            for (uint32_t w = threadIdx.x; w < nw_cta; w += NT) {
-                uint32_t C = 0;
-                const uint32_t j0 = 32 * w;
-                if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);
-                if (a.has_n4 && w_begin + w == 0) C |= 1u;
-                lw(1)[w] = (uint16_t)w;
-                lc(1)[w] = C;
-            }
-            __syncthreads();
-            best = track_block<NT, 0>(Qc, D0w, lw(1), lc(1), nw_cta, j_cta);
-            if (a.has_n4 && w_begin == 0 && threadIdx.x == 0) {
-                // n = 4 (p_min 2, prime index 0) if nothing larger was found
-                const unsigned long long k4 = (1ull << 32) | 0xffffffffull;
-                if (k4 > best) best = k4;
-            }
-        } else if (NB >= 2 && last_in == 1) {
-            best = track_block<NT, (NB >= 2 ? 64 : 0)>(Qc, D0w, lw(last_list), lc(last_list), last_n, j_cta);
-        } else if (NB >= 3 && last_in == 2) {
-            best = track_block<NT, (NB >= 3 ? 128 : 0)>(Qc, D0w, lw(last_list), lc(last_list), last_n, j_cta);
-        } else if (NB >= 4 && last_in == 3) {
-            best = track_block<NT, (NB >= 4 ? 192 : 0)>(Qc, D0w, lw(last_list), lc(last_list), last_n, j_cta);
+        // every n of the CTA was settled in block 0 (or stayed open): run block
+        // 0 again over every word, recording each word's last covering step
+        best = 0;
+        for (uint32_t w = threadIdx.x; w < nw_cta; w += NT) {
+            uint32_t C = 0;
+            const uint32_t j0 = 32 * w;
+            if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);
+            if (a.has_n4 && w_begin + w == 0) C |= 1u;
+            const unsigned long long key = track_word<0>(Qc, D0w, (uint32_t)w, C, j_cta);
+            if (key > best) best = key;
+        }
+        if (a.has_n4 && w_begin == 0 && threadIdx.x == 0) {
+            // n = 4 (p_min 2, prime index 0) if nothing larger was found
+            const unsigned long long k4 = (1ull << 32) | 0xffffffffull;
+            if (k4 > best) best = k4;
         }
         const uint32_t khi = (uint32_t)(best >> 32);
         const uint32_t mhi = __reduce_max_sync(0xffffffffu, khi);
@@ -512,8 +500,10 @@ static cudaError_t launch_nb(const CoverArgs& a, cudaStream_t s)
     constexpr int NT = 256;
     const unsigned grid = a.nseg * a.chunks_per_seg;
     if (grid == 0) return cudaSuccess;
-    // two lists of the CTA's words: 32-bit coverage, 16-bit index
-    const size_t smem = (size_t)2 * (2 * a.cta_words) * 6;
+    // one list per warp holding every word it takes in block 0: 32-bit
+    // coverage, 16-bit index
+    const uint32_t cap = (2 * a.cta_words + 96 * (NT / 32) - 1) / (96 * (NT / 32)) * 96;
+    const size_t smem = (size_t)(NT / 32) * cap * 6;
     auto k = k_cover_fast<NT, NB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
