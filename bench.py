@@ -303,35 +303,47 @@ def main():
     # ---- roofline of the dominant kernel (per-launch averages over the timed region)
     peaks, peak_src = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    kern = max(("sieve", "cover"), key=lambda k: prof[k]["ms"])
-    kp = prof[kern]
-    launches = max(1, kp["launches"])
-    per_launch_ms = kp["ms"] / launches
-    # integer issue peak: 152 SMs x 4 schedulers x 32 lanes x f_max (lane-ops/s)
-    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12            # T lane-ops/s
-    if kern == "cover":
-        # 4 lane-ops per first-phase (word, prime) step: shift, or, popcount, add;
-        # 4 per second-phase probe: offset load, add, word load, bit test
-        units = work["cover_iterations"]
-        ops = 4.0 * units
-        unit_name = "cover steps (first-phase word steps + second-phase probes), 4 lane-ops each"
-    else:
-        # 4 lane-ops per strike (word index, bit mask, complement, shared atomic AND)
-        # plus 5 per stamped 32-bit word (four pattern reads + store)
-        units = work["sieve_strikes"]
-        ops = 4.0 * units + 5.0 * kp["units"] / 32.0
-        unit_name = "sieve strikes (4 lane-ops) + stamped words (5 lane-ops)"
-    achieved = (ops / launches) / (per_launch_ms / 1000.0) / 1e12
-    hbm_bytes = (kp["units"] / launches) / 8.0            # q bits written (sieve) or n read (cover) / 8
-    hbm_achieved = hbm_bytes / (per_launch_ms / 1000.0) / 1e9
-    roofline = {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "T lane-ops/s", "frac": achieved / alu_peak, "traffic": None,
-                "work": unit_name, "work_units_per_launch": units / launches,
-                "ms_per_launch": per_launch_ms,
-                "peak_source": "derived: 152 SMs x 128 lanes x %.0f MHz (%s max clock)" % (sm_max, peak_src),
-                "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
-                        "frac": hbm_achieved / float(peaks.get("hbm_gbs", 6800.0)),
-                        "algorithmic_bytes_per_launch": hbm_bytes}}
+    # Both hot kernels are bound by the SM's integer ALU pipe (shifts and
+    # logic ops; ncu shows it near saturation).  Its peak, from the unit counts
+    # and clock: 152 SMs x 64 ALU lanes per cycle (16 per scheduler: half the
+    # issue rate, measured by a shift/or loop) x the maximum SM clock.
+    alu_peak = 152 * 64 * sm_max * 1e6 / 1e12            # T ALU lane-ops/s
+    per = {}
+    for kern in ("sieve", "cover"):
+        kp = prof[kern]
+        launches = max(1, kp["launches"])
+        ms = kp["ms"] / launches
+        if kern == "cover":
+            # minimal ALU work: 2 ops per (32-bit coverage word, prime) step,
+            # the funnel shift that aligns the partner bits and the OR into C;
+            # 2 per probed (n, prime): shift and bit test
+            units = work["cover_iterations"] / launches
+            ops = 2.0 * units
+            # DRAM bytes per even n measured by ncu on [4, 2^32] (profiles/):
+            # the q window read once; scaled to this launch's n
+            traffic = 0.1269 * kp["units"] / launches
+            alg_bytes = kp["units"] / launches / 8.0
+        else:
+            # minimal ALU work: 2 ops per strike (word index, rotated mask) and
+            # 6 per stamped 32-bit word (four pattern funnel shifts, two ANDs)
+            units = work["sieve_strikes"] / launches
+            ops = 2.0 * units + 6.0 * (kp["units"] / launches) / 32.0
+            traffic = 0.09657 * kp["units"] / launches   # ncu bytes per q bit (written once)
+            alg_bytes = kp["units"] / launches / 8.0
+        achieved = ops / (ms / 1000.0) / 1e12
+        per[kern] = {"ms_per_launch": ms, "achieved": achieved, "frac": achieved / alu_peak,
+                     "alu_ops_per_launch": ops, "work_units_per_launch": units,
+                     "dram_bytes_per_launch": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+                     "hbm_frac": (alg_bytes / (ms / 1000.0)) / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)}
+    kern = max(per, key=lambda k: per[k]["ms_per_launch"])
+    roofline = {"kernel": kern, "bound": "alu", "achieved": per[kern]["achieved"], "peak": alu_peak,
+                "unit": "T ALU lane-ops/s", "frac": per[kern]["frac"],
+                "traffic": per[kern]["dram_bytes_per_launch"],
+                "peak_source": "derived: 152 SMs x 64 ALU lanes x %.0f MHz (%s max clock)" % (sm_max, peak_src),
+                "work": ("cover: 2 ALU ops per (coverage word, prime) step and per probe; "
+                         "sieve: 2 per strike + 6 per stamped word"),
+                "kernels": per,
+                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
