@@ -149,6 +149,33 @@ int gb_prime_pi(gb_ctx* ctx, uint64_t x, uint64_t* count);
 int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P,
                     gb_range_result* out);
 
+/* gb_verify_range without memory allocation (the paper has no counterpart:
+ * this is a calling convention of this library).  Some callers must not call
+ * cudaMalloc while they run -- it can synchronize the device and stall every
+ * stream, which a latency-bound request loop sharing the GPU cannot afford,
+ * and a caller working inside a memory budget granted up front may not
+ * allocate at all.  gb_verify_range may grow the context's device arenas on
+ * a call; this entry point never allocates: its per-call scratch is one
+ * file-scope device array of GB_NOALLOC_SCRATCH_BYTES, which every GPU that
+ * loads the library holds until the process exits.
+ *
+ * Same arguments, outputs and results as gb_verify_range, with these limits
+ * (beyond them: GB_ERANGE, nothing computed):
+ *   - at most GB_NOALLOC_MAX_N even n, all in one segment (n <= seg_len);
+ *   - final bound max(P, p2) at most GB_NOALLOC_MAX_P;
+ *   - seg_hist_stride at most GB_NOALLOC_MAX_STRIDE;
+ *   - out->pmin, if given, must be device memory (GB_EINVAL otherwise).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: each clears what must start at zero, and
+ * calls whose work overlaps on the GPU (other streams, other threads) race. */
+#define GB_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define GB_NOALLOC_MAX_N         (1u << 22)
+#define GB_NOALLOC_MAX_P         (1u << 20)
+#define GB_NOALLOC_MAX_STRIDE    (1u << 17)
+int gb_verify_range_noalloc(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P,
+                            gb_range_result* out);
+
 /* Per-kernel device time, measured with CUDA events recorded on the
  * context's stream around every launch while profiling is enabled.  Kinds:
  * 0 segment sieve (units: q bits sieved), 1 cover (units: even n), 2 retry

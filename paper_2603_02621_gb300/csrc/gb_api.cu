@@ -296,6 +296,32 @@ int build_primes(gb_ctx* ctx)
     return GB_OK;
 }
 
+}  // namespace
+
+// accessors for entry points in other translation units
+namespace gb {
+int ctx_view(const gb_ctx* ctx, CtxView* v)
+{
+    if (!ctx || !v) return fail(GB_EINVAL, "NULL argument");
+    v->device = ctx->cfg.device;
+    v->stream = ctx->stream;
+    v->L = ctx->L;
+    v->seg_len = ctx->cfg.seg_len;
+    v->p1 = ctx->cfg.p1;
+    v->p2 = ctx->cfg.p2;
+    v->cta_threads = ctx->cfg.cta_threads;
+    v->primes = ctx->primes.as<uint32_t>();
+    v->generic_cover = ctx->generic_cover;
+    v->ka_override = ctx->ka_override;
+    return GB_OK;
+}
+uint64_t ctx_pi(const gb_ctx* ctx, uint64_t x) { return ctx->pi(x); }
+int ctx_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out) { return run_sieve(ctx, B, nbits, out, nullptr); }
+int set_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace gb
+
+namespace {
+
 bool is_device_ptr(const void* p)
 {
     cudaPointerAttributes at{};

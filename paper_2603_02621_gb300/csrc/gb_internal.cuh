@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+typedef struct gb_ctx gb_ctx;
+
 namespace gb {
 
 // ---------------------------------------------------------------------------
@@ -197,5 +199,21 @@ struct FinalizeArgs {
     RangeTotals* totals;
 };
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+
+// Read-only view of a context for entry points defined outside gb_api.cu.
+struct CtxView {
+    int device;
+    cudaStream_t stream;
+    uint64_t L;                 // primes known up to L
+    uint32_t seg_len, p1, p2, cta_threads;
+    const uint32_t* primes;     // device [2, 3, 5, ...]
+    bool generic_cover;
+    int ka_override;
+};
+int ctx_view(const gb_ctx* ctx, CtxView* v);
+uint64_t ctx_pi(const gb_ctx* ctx, uint64_t x);            // primes <= x (x <= L)
+// segment sieve of the odd numbers B + 2i, i < nbits, into out (device words)
+int ctx_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out);
+int set_error(int code, const char* msg);                 // records gb_last_error()
 
 }  // namespace gb

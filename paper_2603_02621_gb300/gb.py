@@ -58,6 +58,7 @@ SIGNATURES = {
     "gb_sieve_segment": (c_int, [c_void_p, c_int64, c_uint64, c_void_p, POINTER(c_uint64)]),
     "gb_prime_pi": (c_int, [c_void_p, c_uint64, POINTER(c_uint64)]),
     "gb_verify_range": (c_int, [c_void_p, c_uint64, c_uint64, c_uint32, POINTER(gb_range_result)]),
+    "gb_verify_range_noalloc": (c_int, [c_void_p, c_uint64, c_uint64, c_uint32, POINTER(gb_range_result)]),
     "gb_profile_enable": (c_int, [c_void_p, c_int]),
     "gb_profile_read": (c_int, [c_void_p, POINTER(ctypes.c_double), POINTER(c_uint64), POINTER(c_uint64)]),
     "gb_profile_work": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64)]),
@@ -159,6 +160,22 @@ def gb_verify_range(ctx: int, lo: int, hi: int, P: int = 0, *, hist_cap: int = 0
     'hist' (np.uint64[hist_cap]), 'segs' (structured rows), 'seg_hist'
     (np.uint64[nseg, stride]) when asked.  pmin: optional uint32 buffer of
     (hi-lo)/2 entries, host (numpy / CPU tensor) or device (CUDA tensor)."""
+    return _verify(load().gb_verify_range, "gb_verify_range", ctx, lo, hi, P, hist_cap=hist_cap,
+                   pmin=pmin, segs=segs, seg_hist_stride=seg_hist_stride, allow_erange=allow_erange)
+
+
+def gb_verify_range_noalloc(ctx: int, lo: int, hi: int, P: int = 0, *, hist_cap: int = 0,
+                            pmin=None, segs: bool = False, seg_hist_stride: int = 0,
+                            allow_erange: bool = False) -> dict:
+    """gb_verify_range for callers that must not allocate device memory during
+    the call: one segment of at most GB_NOALLOC_MAX_N even n, scratch in a
+    fixed device array of the library; pmin (if any) must be device memory."""
+    return _verify(load().gb_verify_range_noalloc, "gb_verify_range_noalloc", ctx, lo, hi, P,
+                   hist_cap=hist_cap, pmin=pmin, segs=segs, seg_hist_stride=seg_hist_stride,
+                   allow_erange=allow_erange)
+
+
+def _verify(fn, name, ctx, lo, hi, P, *, hist_cap, pmin, segs, seg_hist_stride, allow_erange):
     lib = load()
     r = gb_range_result()
     out = {}
@@ -181,8 +198,7 @@ def gb_verify_range(ctx: int, lo: int, hi: int, P: int = 0, *, hist_cap: int = 0
         rows = np.zeros((nseg, seg_hist_stride), dtype=np.uint64)
         r.seg_hist = rows.ctypes.data_as(POINTER(c_uint64))
         r.seg_hist_stride = seg_hist_stride
-    rc = _check(lib.gb_verify_range(ctx, lo, hi, P, ctypes.byref(r)), "gb_verify_range",
-                allow=(GB_ERANGE,) if allow_erange else ())
+    rc = _check(fn(ctx, lo, hi, P, ctypes.byref(r)), name, allow=(GB_ERANGE,) if allow_erange else ())
     out.update(rc=rc, n_checked=r.n_checked, unresolved=r.unresolved, max_pmin=r.max_pmin,
                max_pmin_n=r.max_pmin_n, hist_len=r.hist_len, n_segments=r.n_segments,
                p_final=r.p_final)
@@ -265,3 +281,6 @@ class Context:
 
     def verify_range(self, lo, hi, P=0, **kw):
         return gb_verify_range(self.handle, lo, hi, P, **kw)
+
+    def verify_range_noalloc(self, lo, hi, P=0, **kw):
+        return gb_verify_range_noalloc(self.handle, lo, hi, P, **kw)
