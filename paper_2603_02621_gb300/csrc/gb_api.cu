@@ -106,6 +106,7 @@ struct gb_ctx {
     uint64_t work_strikes = 0, work_iters = 0;
     int warp_split = 0;               // sieving primes below this strike one warp each
     bool generic_cover = false;       // force the generic cover kernel (GB_COVER=generic)
+    uint64_t large_chunk_bits = 1ull << 30;   // large-prime strikes per L2-sized chunk of the window
     int ka_override = 0;              // first-phase length of the two-phase cover (GB_KA)
 
     // per-kernel device time (CUDA events on the context's stream around each launch)
@@ -211,22 +212,44 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
     const uint64_t r = last > 0 ? isqrt_u64((uint64_t)last) : 0;
     if (r > ctx->L) return fail(GB_EINVAL, "window beyond base_limit^2");
     const uint64_t np = ctx->pi(r);                 // primes <= sqrt(last)
+    // primes from bucket_split on are struck by the large-prime kernel, chunk
+    // by chunk, into the output words (the tile kernel only counts bits when
+    // there are none)
+    const uint64_t nsmall = std::min<uint64_t>(np, std::max<uint64_t>(ctx->pi(ctx->cfg.bucket_split - 1), gb::kFirstStrikeIdx));
+    const bool large = np > nsmall && out;
+    if (np > nsmall && !out) return fail(GB_EINVAL, "internal: large primes need an output buffer");
     gb::SieveArgs a{};
     a.B = B;
     a.nbits = nbits;
     a.tile_bits = ctx->cfg.tile_bits;
     a.primes = ctx->primes.as<uint32_t>() + gb::kFirstStrikeIdx;
     a.recip = ctx->recip.as<uint64_t>() + gb::kFirstStrikeIdx;
-    const uint64_t nstrike = np > gb::kFirstStrikeIdx ? np - gb::kFirstStrikeIdx : 0;
+    const uint64_t nstrike = nsmall > gb::kFirstStrikeIdx ? nsmall - gb::kFirstStrikeIdx : 0;
     const uint64_t nwarp = std::min<uint64_t>(nstrike, ctx->pi((uint64_t)ctx->warp_split - 1) > gb::kFirstStrikeIdx
                                                             ? ctx->pi((uint64_t)ctx->warp_split - 1) - gb::kFirstStrikeIdx : 0);
     a.n_warp = (uint32_t)nwarp;
     a.n_primes = (uint32_t)nstrike;
     a.wheel = ctx->wheel.as<uint32_t>();
     a.out = out;
-    a.popcount = popc;
+    a.popcount = large ? nullptr : popc;
     a.strikes = ctx->work_ptr(0);
     GB_CUDA(gb::launch_sieve(a, (int)ctx->cfg.cta_threads, ctx->stream));
+    if (large) {
+        gb::LargeArgs la{};
+        la.B = B;
+        la.primes = ctx->primes.as<uint32_t>() + nsmall;
+        la.recip = ctx->recip.as<uint64_t>() + nsmall;
+        la.n_primes = (uint32_t)(np - nsmall);
+        la.out = out;
+        la.strikes = ctx->work_ptr(0);
+        const uint64_t chunk = ctx->large_chunk_bits;
+        for (uint64_t c0 = 0; c0 < nbits; c0 += chunk) {
+            la.bit_lo = c0;
+            la.bit_hi = std::min(nbits, c0 + chunk);
+            GB_CUDA(gb::launch_large(la, ctx->stream));
+        }
+        if (popc) GB_CUDA(gb::launch_popcount(out, ((nbits + 63) / 64) * 2, popc, ctx->stream));
+    }
     return GB_OK;
 }
 
@@ -382,6 +405,10 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     ctx->warp_split = (int)std::min<uint32_t>(1024, c.tile_bits / 64);
     if (const char* e = getenv("GB_WARP_SPLIT")) ctx->warp_split = atoi(e);
     if (const char* e = getenv("GB_COVER")) ctx->generic_cover = std::string(e) == "generic";
+    if (const char* e = getenv("GB_LARGE_CHUNK_LOG2")) {
+        const int v = atoi(e);
+        if (v >= 16 && v <= 40) ctx->large_chunk_bits = 1ull << v;
+    }
     if (const char* e = getenv("GB_KA")) {
         const int v = atoi(e);
         if (v == 64 || v == 128 || v == 192 || v == 256) ctx->ka_override = v;
@@ -450,9 +477,13 @@ int gb_prime_pi(gb_ctx* ctx, uint64_t x, uint64_t* count)
     GB_CUDA(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
     const uint64_t total = (x - 1) / 2;             // odd numbers 3 .. x
     const uint64_t chunk = ctx->cfg.slab_bits;
+    // primes from bucket_split on strike into a buffer, so sieve into the slab buffer
+    const bool need_buf = ctx->pi(isqrt_u64(x)) > ctx->pi(ctx->cfg.bucket_split - 1);
+    if (need_buf && (rc = ctx->q.ensure(((std::min(chunk, total) + 63) / 64) * 8))) return rc;
     for (uint64_t done = 0; done < total; done += chunk) {
         const uint64_t nb = std::min(chunk, total - done);
-        rc = run_sieve(ctx, 3 + 2 * (int64_t)done, nb, nullptr, ctx->counter.as<unsigned long long>());
+        rc = run_sieve(ctx, 3 + 2 * (int64_t)done, nb, need_buf ? ctx->q.as<uint32_t>() : nullptr,
+                       ctx->counter.as<unsigned long long>());
         if (rc) return rc;
     }
     unsigned long long c = 0;

@@ -73,6 +73,23 @@ struct SieveArgs {
     unsigned long long* strikes;    // optional: number of bits struck (work count)
 };
 
+// Strikes of the primes larger than a tile: one thread per prime, every odd
+// multiple (>= p^2) in the bit range [bit_lo, bit_hi) of the window starting at
+// the odd number B, cleared in place with global atomic AND.  Launched per
+// chunk of the window small enough to stay in L2.
+struct LargeArgs {
+    int64_t  B;                 // odd number of bit 0 of the window
+    uint64_t bit_lo, bit_hi;    // chunk of the window to strike
+    const uint32_t* primes;     // the large primes
+    const uint64_t* recip;      // their Barrett reciprocals
+    uint32_t n_primes;
+    uint32_t* out;              // window words
+    unsigned long long* strikes;    // optional work count
+};
+cudaError_t launch_large(const LargeArgs& a, cudaStream_t s);
+// population count of n 32-bit words, added to *count
+cudaError_t launch_popcount(const uint32_t* words, uint64_t n, unsigned long long* count, cudaStream_t s);
+
 cudaError_t launch_wheel_tables(uint32_t* wheel /*kWheelWords*/, cudaStream_t s);
 cudaError_t launch_seed_sieve(uint32_t* words /*1024*/, cudaStream_t s);
 cudaError_t launch_sieve(const SieveArgs& a, int threads, cudaStream_t s);

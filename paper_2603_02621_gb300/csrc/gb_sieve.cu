@@ -276,6 +276,65 @@ cudaError_t launch_sieve(const SieveArgs& a, int threads, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
+// primes larger than a tile: each hits a tile at most once, so the tile kernel
+// would spend a Barrett start per (tile, prime) for at most one strike.  Here
+// one thread takes one prime for a whole chunk of the window (one Barrett
+// start per chunk) and clears its multiples in global memory with atomic AND;
+// a chunk of 2^30 bits (128 MB) keeps the struck words in the 126 MB L2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_large(const LargeArgs a)
+{
+    const int64_t b = a.B + 2 * (int64_t)a.bit_lo;          // number of the chunk's first bit
+    const int64_t last = a.B + 2 * (int64_t)(a.bit_hi - 1);
+    const uint64_t span = a.bit_hi - a.bit_lo;
+    unsigned long long nstrike = 0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_primes; k += gridDim.x * blockDim.x) {
+        const uint32_t p = a.primes[k];
+        const uint64_t pp = (uint64_t)p * p;
+        if ((int64_t)pp > last) continue;
+        uint64_t i = first_odd_multiple(b, p, a.recip[k]);
+        if ((int64_t)pp > b) {
+            const uint64_t isq = ((uint64_t)((int64_t)pp - b)) >> 1;
+            if (isq > i) i = isq;
+        }
+        for (; i < span; i += p) {
+            const uint64_t bit = a.bit_lo + i;
+            atomicAnd(a.out + (bit >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, (uint32_t)bit));
+            ++nstrike;
+        }
+    }
+    if (a.strikes) {
+        for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);
+        if ((threadIdx.x & 31) == 0 && nstrike) atomicAdd(a.strikes, nstrike);
+    }
+}
+
+cudaError_t launch_large(const LargeArgs& a, cudaStream_t s)
+{
+    if (a.n_primes == 0 || a.bit_hi <= a.bit_lo) return cudaSuccess;
+    const uint32_t grid = (a.n_primes + 255) / 256 < 152u * 64 ? (a.n_primes + 255) / 256 : 152u * 64;
+    k_large<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_popcount(const uint32_t* w, uint64_t n, unsigned long long* count)
+{
+    unsigned long long c = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        c += __popc(w[i]);
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+cudaError_t launch_popcount(const uint32_t* words, uint64_t n, unsigned long long* count, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + 255) / 256;
+    k_popcount<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(words, n, count);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // compaction: bitset -> ascending prime list (after a leading 2) + reciprocals
 // ---------------------------------------------------------------------------
 constexpr uint32_t kCompactChunk = 8192;   // words per CTA
