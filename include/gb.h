@@ -149,6 +149,22 @@ int gb_prime_pi(gb_ctx* ctx, uint64_t x, uint64_t* count);
 int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P,
                     gb_range_result* out);
 
+/* Batched verification: count independent ranges [lo[i], hi[i]) verified in
+ * one pass of persistent kernels (the segment loop of Sec. 2.3 over many
+ * ranges at once; the work queue and the per-range windows let thousands of
+ * ranges of uneven length share the GPU).  Each range gets the outputs
+ * gb_verify_range would give it: one record in
+ * results[i] (lo, hi, n_checked, unresolved, max_pmin with its smallest n,
+ * hist_len) and, if hist is given, row i (hist_stride entries) of its p_min
+ * histogram.  P as in gb_verify_range (0: the context's p1); a range with n
+ * still open after P is redone by gb_verify_range, retry pass included, so
+ * the results equal calling gb_verify_range on each range.  lo/hi: host
+ * arrays; results and hist: host or device.  Each range needs
+ * hi - lo <= 2 * 2^32 and hi <= base_limit^2; count <= 2^24.  GB_ERANGE if a
+ * range's hist_len exceeds hist_stride (the row is truncated). */
+int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_t count, uint32_t P,
+                    gb_segment_result* results, uint64_t* hist, uint32_t hist_stride);
+
 /* gb_verify_range without memory allocation (the paper has no counterpart:
  * this is a calling convention of this library).  Some callers must not call
  * cudaMalloc while they run -- it can synchronize the device and stall every

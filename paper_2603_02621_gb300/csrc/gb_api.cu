@@ -81,6 +81,34 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// grow-only pinned host buffer (staging of batch descriptors and results)
+struct HostBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t bytes)
+    {
+        if (bytes <= cap) return GB_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = bytes + bytes / 8 + 4096;
+        const cudaError_t e = cudaMallocHost(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GB_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+        }
+        cap = want;
+        return GB_OK;
+    }
+    HostBuf() = default;
+    HostBuf(const HostBuf&) = delete;
+    HostBuf& operator=(const HostBuf&) = delete;
+    ~HostBuf()
+    {
+        if (p) cudaFreeHost(p);
+    }
+};
+
 uint64_t isqrt_u64(uint64_t x)
 {
     uint64_t r = 0;
@@ -103,10 +131,13 @@ struct gb_ctx {
     DevBuf q;                         // slab q window
     DevBuf hist, maxkey, maxkey2, unres, retry, retry_count, summary, rows, merged, pmin, counter, totals, records;
     DevBuf work;                      // profiling work counters: [0] sieve strikes, [1] cover iterations
+    // batched mode
+    DevBuf bq, bhist, bkeys, bunres, bdesc, brecords, brows;
+    HostBuf hstage;
     uint64_t work_strikes = 0, work_iters = 0;
     int warp_split = 0;               // sieving primes below this strike one warp each
     bool generic_cover = false;       // force the generic cover kernel (GB_COVER=generic)
-    uint64_t large_chunk_bits = 1ull << 30;   // large-prime strikes per L2-sized chunk of the window
+    uint64_t large_chunk_bits = 1ull << 28;   // large-prime strikes per L2-resident chunk of the window
     int ka_override = 0;              // first-phase length of the two-phase cover (GB_KA)
 
     // per-kernel device time (CUDA events on the context's stream around each launch)
@@ -333,9 +364,15 @@ int ctx_view(const gb_ctx* ctx, CtxView* v)
     v->p1 = ctx->cfg.p1;
     v->p2 = ctx->cfg.p2;
     v->cta_threads = ctx->cfg.cta_threads;
+    v->tile_bits = ctx->cfg.tile_bits;
+    v->bucket_split = ctx->cfg.bucket_split;
+    v->warp_split = (uint32_t)ctx->warp_split;
     v->primes = ctx->primes.as<uint32_t>();
+    v->recip = ctx->recip.as<uint64_t>();
+    v->wheel = ctx->wheel.as<uint32_t>();
     v->generic_cover = ctx->generic_cover;
     v->ka_override = ctx->ka_override;
+    v->large_chunk_bits = ctx->large_chunk_bits;
     return GB_OK;
 }
 uint64_t ctx_pi(const gb_ctx* ctx, uint64_t x) { return ctx->pi(x); }
@@ -430,7 +467,8 @@ void gb_destroy(gb_ctx* ctx)
     else cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->primes, &ctx->recip, &ctx->wheel, &ctx->q, &ctx->hist,
                       &ctx->maxkey, &ctx->maxkey2, &ctx->unres, &ctx->retry, &ctx->retry_count, &ctx->summary,
-                      &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work};
+                      &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work,
+                      &ctx->bq, &ctx->bhist, &ctx->bkeys, &ctx->bunres, &ctx->bdesc, &ctx->brecords, &ctx->brows};
     for (DevBuf* b : bufs) b->release();
     delete ctx;
 }
@@ -717,6 +755,235 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         }
     }
     if (erange) return fail(GB_ERANGE, "an output buffer was too small; what fit was written");
+    return GB_OK;
+}
+
+int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_t count, uint32_t P,
+                    gb_segment_result* results, uint64_t* hist, uint32_t hist_stride)
+{
+    if (!ctx || (count && (!lo || !hi || !results))) return fail(GB_EINVAL, "NULL argument");
+    if (count == 0) return GB_OK;
+    if (count > (1u << 24)) return fail(GB_EINVAL, "count above 2^24");
+    const gb_config& cfg = ctx->cfg;
+    const uint32_t P1 = P ? P : cfg.p1;
+    if (P1 < 2 || P1 > (1u << 24) || P1 > ctx->L) return fail(GB_EINVAL, "P out of range (2 .. min(2^24, base list))");
+    const uint32_t K1 = (uint32_t)(ctx->pi(P1) - 1);
+    const uint32_t H = 64 * ((P1 + 1 - 4 + 63) / 64) + 4;     // first-pass halo
+    const uint32_t hs = K1 + 1;                               // device histogram row
+    const uint32_t T = cfg.tile_bits;
+    const uint32_t cw = 3840;                                 // block-cover CTA chunk (64-bit words)
+    GB_CUDA(cudaSetDevice(cfg.device));
+    cudaStream_t s = ctx->stream;
+
+    // per-range windows and work items
+    uint64_t qwords = 0, n_sieve = 0, n_cover = 0, hi_max = 0, last_max = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        if ((lo[i] & 1) || (hi[i] & 1) || lo[i] < 4 || hi[i] <= lo[i] || hi[i] > (1ull << 63))
+            return fail(GB_EINVAL, "range must be even, lo >= 4, hi > lo");
+        const uint64_t n = (hi[i] - lo[i]) / 2;
+        if (n > (1ull << 32)) return fail(GB_EINVAL, "a batch range holds at most 2^32 even n");
+        const uint64_t qw = (n + 63) / 64 + H / 128 + 2;
+        qwords += qw;
+        n_sieve += (64 * qw + T - 1) / T;
+        n_cover += (((n + 31) / 32) + 2ull * cw - 1) / (2ull * cw);
+        hi_max = std::max(hi_max, hi[i]);
+        last_max = std::max(last_max, lo[i] - H + 1 + 2 * (64 * qw - 1));   // window's last number
+    }
+    if (isqrt_u64(last_max) > ctx->L) return fail(GB_EINVAL, "hi beyond base_limit^2");
+    if (n_sieve > 0xffffffffull || n_cover > 0xffffffffull) return fail(GB_EINVAL, "batch too large");
+
+    // large primes and their groups of ranges (windows of a group fit in L2)
+    const uint64_t np = ctx->pi(isqrt_u64(last_max));
+    const uint64_t nsmall = std::min<uint64_t>(np, std::max<uint64_t>(ctx->pi(cfg.bucket_split - 1), gb::kFirstStrikeIdx));
+    std::vector<uint32_t> groups;
+    {
+        uint64_t acc = 0;
+        groups.push_back(0);
+        for (uint32_t i = 0; i < count; ++i) {
+            const uint64_t qb = 64 * ((hi[i] - lo[i]) / 2 / 64 + H / 128 + 3);
+            if (acc && acc + qb > ctx->large_chunk_bits) {
+                groups.push_back(i);
+                acc = 0;
+            }
+            acc += qb;
+        }
+        groups.push_back(count);
+    }
+    const uint32_t n_groups = (uint32_t)groups.size() - 1;
+
+    // device buffers
+    const size_t desc_ranges = (size_t)count * sizeof(gb::BatchRange);
+    const size_t desc_bytes = desc_ranges + (size_t)(2 * n_sieve + 2 * n_cover) * 4 + (size_t)(n_groups + 1) * 4 + 64;
+    const bool want_rows = hist && hist_stride;
+    const bool res_dev = is_device_ptr(results);
+    const bool rows_dev = want_rows && is_device_ptr(hist);
+    int rc;
+    if ((rc = ctx->bq.ensure(qwords * 8)) || (rc = ctx->bhist.ensure((size_t)count * hs * 4)) ||
+        (rc = ctx->bkeys.ensure((size_t)count * 8)) || (rc = ctx->bunres.ensure((size_t)count * 8)) ||
+        (rc = ctx->bdesc.ensure(desc_bytes)) || (rc = ctx->hstage.ensure(desc_bytes)) ||
+        (!res_dev && (rc = ctx->brecords.ensure((size_t)count * sizeof(gb::SegRecord)))) ||
+        (want_rows && !rows_dev && (rc = ctx->brows.ensure((size_t)count * hist_stride * 8))) ||
+        (rc = ctx->counter.ensure(16)))
+        return rc;
+
+    // descriptors, staged in pinned memory: ranges | sieve items | cover items | groups | counts
+    unsigned char* hs_p = static_cast<unsigned char*>(ctx->hstage.p);
+    gb::BatchRange* hr = reinterpret_cast<gb::BatchRange*>(hs_p);
+    uint32_t* s_range = reinterpret_cast<uint32_t*>(hs_p + desc_ranges);
+    uint32_t* s_tile = s_range + n_sieve;
+    uint32_t* c_range = s_tile + n_sieve;
+    uint32_t* c_chunk = c_range + n_cover;
+    uint32_t* g_first = c_chunk + n_cover;
+    uint32_t* counts = g_first + n_groups + 1;               // [0] sieve items, [1] cover items, [2] ranges
+    {
+        uint64_t off = 0, si = 0, ci = 0;
+        for (uint32_t i = 0; i < count; ++i) {
+            const uint64_t n = (hi[i] - lo[i]) / 2;
+            const uint64_t qw = (n + 63) / 64 + H / 128 + 2;
+            hr[i].lo = lo[i];
+            hr[i].n = n;
+            hr[i].B = (int64_t)lo[i] - (int64_t)H + 1;
+            hr[i].nbits = 64 * qw;
+            hr[i].q_off = off;
+            off += qw;
+            const uint64_t tiles = (64 * qw + T - 1) / T;
+            for (uint64_t t = 0; t < tiles; ++t) { s_range[si] = i; s_tile[si] = (uint32_t)t; ++si; }
+            const uint64_t chunks = (((n + 31) / 32) + 2ull * cw - 1) / (2ull * cw);
+            for (uint64_t c = 0; c < chunks; ++c) { c_range[ci] = i; c_chunk[ci] = (uint32_t)c; ++ci; }
+        }
+        for (uint32_t g = 0; g <= n_groups; ++g) g_first[g] = groups[g];
+        counts[0] = (uint32_t)n_sieve;
+        counts[1] = (uint32_t)n_cover;
+        counts[2] = count;
+    }
+    unsigned char* dd = static_cast<unsigned char*>(ctx->bdesc.p);
+    const size_t used = reinterpret_cast<unsigned char*>(counts + 4) - hs_p;
+    GB_CUDA(cudaMemcpyAsync(dd, hs_p, used, cudaMemcpyHostToDevice, s));
+    const gb::BatchRange* d_ranges = reinterpret_cast<const gb::BatchRange*>(dd);
+    const uint32_t* d_s_range = reinterpret_cast<const uint32_t*>(dd + desc_ranges);
+    const uint32_t* d_s_tile = d_s_range + n_sieve;
+    const uint32_t* d_c_range = d_s_tile + n_sieve;
+    const uint32_t* d_c_chunk = d_c_range + n_cover;
+    const uint32_t* d_groups = d_c_chunk + n_cover;
+    const uint32_t* d_counts = d_groups + n_groups + 1;
+
+    unsigned int* heads = ctx->counter.as<unsigned int>();
+    GB_CUDA(cudaMemsetAsync(heads, 0, 16, s));
+    GB_CUDA(cudaMemsetAsync(ctx->bhist.p, 0, (size_t)count * hs * 4, s));
+    GB_CUDA(cudaMemsetAsync(ctx->bkeys.p, 0, (size_t)count * 8, s));
+    GB_CUDA(cudaMemsetAsync(ctx->bunres.p, 0, (size_t)count * 8, s));
+
+    // sieve: tile part (persistent, item queue), then large primes group by group
+    gb::SieveItemsArgs sa{};
+    sa.base.tile_bits = T;
+    sa.base.primes = ctx->primes.as<uint32_t>() + gb::kFirstStrikeIdx;
+    sa.base.recip = ctx->recip.as<uint64_t>() + gb::kFirstStrikeIdx;
+    const uint64_t nstrike = nsmall > gb::kFirstStrikeIdx ? nsmall - gb::kFirstStrikeIdx : 0;
+    const uint64_t nwarp_all = ctx->pi((uint64_t)ctx->warp_split - 1);
+    sa.base.n_warp = (uint32_t)std::min<uint64_t>(nstrike, nwarp_all > gb::kFirstStrikeIdx ? nwarp_all - gb::kFirstStrikeIdx : 0);
+    sa.base.n_primes = (uint32_t)nstrike;
+    sa.base.wheel = ctx->wheel.as<uint32_t>();
+    sa.base.strikes = ctx->work_ptr(0);
+    sa.ranges = d_ranges;
+    sa.item_range = d_s_range;
+    sa.item_tile = d_s_tile;
+    sa.n_items = d_counts + 0;
+    sa.head = heads + 0;
+    sa.Q = ctx->bq.as<uint32_t>();
+    ctx->prof_begin(kProfSieve, qwords * 64);
+    GB_CUDA(gb::launch_sieve_items(sa, (int)cfg.cta_threads, s));
+    if (np > nsmall) {
+        gb::LargeBatchArgs la{};
+        la.ranges = d_ranges;
+        la.groups = d_groups;
+        la.primes = ctx->primes.as<uint32_t>() + nsmall;
+        la.recip = ctx->recip.as<uint64_t>() + nsmall;
+        la.n_primes = (uint32_t)(np - nsmall);
+        la.Q = ctx->bq.as<uint32_t>();
+        la.strikes = ctx->work_ptr(0);
+        for (uint32_t g = 0; g < n_groups; ++g) {
+            la.group = g;
+            GB_CUDA(gb::launch_large_batch(la, s));
+        }
+    }
+    ctx->prof_end();
+
+    // cover: persistent, item queue; row r = range r; no retry here
+    int KA = ctx->generic_cover ? 0 : gb::cover_fast_phase_primes(K1, hi_max);
+    if (KA && ctx->ka_override && (uint32_t)ctx->ka_override <= K1) KA = ctx->ka_override;
+    if (!KA) return fail(GB_EINVAL, "gb_verify_batch needs P >= the 64th odd prime (313)");
+    gb::CoverItemsArgs cv{};
+    cv.base.H = H;
+    cv.base.cta_words = cw;
+    cv.base.primes = ctx->primes.as<uint32_t>();
+    cv.base.K = K1;
+    cv.base.hist_stride = hs;
+    cv.base.hist = ctx->bhist.as<uint32_t>();
+    cv.base.maxkey = ctx->bkeys.as<unsigned long long>();
+    cv.base.unresolved = ctx->bunres.as<unsigned long long>();
+    cv.base.iters = ctx->work_ptr(1);
+    cv.ranges = d_ranges;
+    cv.item_range = d_c_range;
+    cv.item_chunk = d_c_chunk;
+    cv.n_items = d_counts + 1;
+    cv.head = heads + 1;
+    cv.Q = ctx->bq.as<uint64_t>();
+    ctx->prof_begin(kProfCover, qwords * 64);
+    GB_CUDA(gb::launch_cover_items(cv, KA, s));
+    ctx->prof_end();
+
+    gb::ReduceBatchArgs ra{};
+    ra.ranges = d_ranges;
+    ra.count = d_counts + 2;
+    ra.hist = ctx->bhist.as<uint32_t>();
+    ra.hist_stride = hs;
+    ra.maxkey = ctx->bkeys.as<unsigned long long>();
+    ra.unresolved = ctx->bunres.as<unsigned long long>();
+    ra.primes = ctx->primes.as<uint32_t>();
+    ra.records = res_dev ? reinterpret_cast<gb::SegRecord*>(results) : ctx->brecords.as<gb::SegRecord>();
+    ra.rows = want_rows ? (rows_dev ? hist : ctx->brows.as<uint64_t>()) : nullptr;
+    ra.row_stride = want_rows ? hist_stride : 0;
+    ctx->prof_begin(kProfReduce, count);
+    GB_CUDA(gb::launch_reduce_batch(ra, count, s));
+    ctx->prof_end();
+
+    // results to the caller; ranges with open n are redone with the retry pass
+    std::vector<gb::SegRecord> rec(count);
+    GB_CUDA(cudaMemcpyAsync(rec.data(), ra.records, (size_t)count * sizeof(gb::SegRecord), cudaMemcpyDeviceToHost, s));
+    if (want_rows && !rows_dev)
+        GB_CUDA(cudaMemcpyAsync(hist, ctx->brows.p, (size_t)count * hist_stride * 8, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    int status = GB_OK;
+    for (uint32_t i = 0; i < count; ++i) {
+        gb::SegRecord& r = rec[i];
+        if (r.unresolved && cfg.p2 > P1) {
+            // the range's totals and histogram from the plain path (retry pass included)
+            gb_range_result one{};
+            std::vector<uint64_t> row(want_rows ? hist_stride : 0);
+            if (want_rows) {
+                one.hist = row.data();
+                one.hist_cap = hist_stride;
+            }
+            rc = gb_verify_range(ctx, r.lo, r.hi, P1, &one);
+            if (rc && rc != GB_ERANGE) return rc;
+            r.unresolved = one.unresolved;
+            r.max_pmin = one.max_pmin;
+            r.max_pmin_n = one.max_pmin_n;
+            r.hist_len = one.hist_len;
+            if (res_dev)
+                GB_CUDA(cudaMemcpy(reinterpret_cast<gb::SegRecord*>(results) + i, &r, sizeof r, cudaMemcpyHostToDevice));
+            if (want_rows) {
+                if (rows_dev)
+                    GB_CUDA(cudaMemcpy(hist + (uint64_t)i * hist_stride, row.data(), (size_t)hist_stride * 8,
+                                       cudaMemcpyHostToDevice));
+                else
+                    std::memcpy(hist + (uint64_t)i * hist_stride, row.data(), (size_t)hist_stride * 8);
+            }
+        }
+        if (want_rows && r.hist_len > hist_stride) status = GB_ERANGE;
+    }
+    if (!res_dev) std::memcpy(results, rec.data(), (size_t)count * sizeof(gb::SegRecord));
+    if (status == GB_ERANGE) return fail(GB_ERANGE, "a histogram row was longer than hist_stride");
     return GB_OK;
 }
 

@@ -1,0 +1,87 @@
+// gb_batch.cu -- kernels of the batched mode: many ranges of uneven length and
+// offset verified in one pass (GoldbachGPU, arXiv 2603.02621: the segment
+// loop of Sec. 2.3, here over many independent ranges at once).
+//
+// The batch lays every range's q window end to end in one buffer.  The tile
+// sieve and the block cover run as persistent kernels over (range, tile) and
+// (range, chunk) items (gb_sieve.cu, gb_cover_fast.cu); this file holds the
+// large-prime strikes over groups of ranges and the per-range reduction.
+#include "gb_internal.cuh"
+
+namespace gb {
+
+// primes above the tile size, over the ranges of one group (the group's windows
+// together fit in L2): one thread per prime, every range of the group
+__global__ void __launch_bounds__(256) k_large_batch(const LargeBatchArgs a)
+{
+    const uint32_t r0 = a.groups[a.group], r1 = a.groups[a.group + 1];
+    unsigned long long nstrike = 0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_primes; k += gridDim.x * blockDim.x) {
+        const uint32_t p = a.primes[k];
+        const uint64_t m = a.recip[k];
+        const uint64_t pp = (uint64_t)p * p;
+        for (uint32_t ri = r0; ri < r1; ++ri) {
+            const BatchRange r = a.ranges[ri];
+            const int64_t last = r.B + 2 * (int64_t)(r.nbits - 1);
+            if ((int64_t)pp > last) continue;
+            uint64_t i = first_odd_multiple(r.B, p, m);
+            if ((int64_t)pp > r.B) {
+                const uint64_t isq = ((uint64_t)((int64_t)pp - r.B)) >> 1;
+                if (isq > i) i = isq;
+            }
+            uint32_t* q = a.Q + 2 * r.q_off;
+            for (; i < r.nbits; i += p) {
+                atomicAnd(q + (i >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, (uint32_t)i));
+                ++nstrike;
+            }
+        }
+    }
+    if (a.strikes) {
+        for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);
+        if ((threadIdx.x & 31) == 0 && nstrike) atomicAdd(a.strikes, nstrike);
+    }
+}
+
+cudaError_t launch_large_batch(const LargeBatchArgs& a, cudaStream_t s)
+{
+    if (a.n_primes == 0) return cudaSuccess;
+    const uint32_t blocks = (a.n_primes + 255) / 256;
+    k_large_batch<<<blocks < 152u * 64 ? blocks : 152u * 64, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// per range: key -> (p, n), uint64 histogram row, record; one CTA per range
+__global__ void __launch_bounds__(256) k_reduce_batch(const ReduceBatchArgs a)
+{
+    const uint32_t ri = blockIdx.x;
+    if (ri >= *a.count) return;
+    const BatchRange r = a.ranges[ri];
+    const unsigned long long key = a.maxkey[ri];
+    const uint32_t pidx1 = (uint32_t)(key >> 32);
+    const uint32_t* hrow = a.hist + (uint64_t)ri * a.hist_stride;
+    if (a.rows) {
+        uint64_t* orow = a.rows + (uint64_t)ri * a.row_stride;
+        for (uint32_t k = threadIdx.x; k < a.row_stride; k += 256)
+            orow[k] = (k < pidx1 && k < a.hist_stride) ? hrow[k] : 0ull;
+    }
+    if (threadIdx.x == 0) {
+        SegRecord rec;
+        rec.lo = r.lo;
+        rec.hi = r.lo + 2 * r.n;
+        rec.n_checked = r.n;
+        rec.unresolved = a.unresolved[ri];
+        rec.max_pmin = pidx1 ? a.primes[pidx1 - 1] : 0u;
+        rec.max_pmin_n = pidx1 ? r.lo + 2 * (0xffffffffull - (key & 0xffffffffull)) : 0ull;
+        rec.hist_len = pidx1;
+        a.records[ri] = rec;
+    }
+}
+
+cudaError_t launch_reduce_batch(const ReduceBatchArgs& a, uint32_t grid, cudaStream_t s)
+{
+    if (grid == 0) return cudaSuccess;
+    k_reduce_batch<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gb

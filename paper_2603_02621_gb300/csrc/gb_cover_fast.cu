@@ -340,31 +340,23 @@ __device__ __forceinline__ void probe_warp(const CoverArgs& a, const uint32_t* Q
 
 // NB unrolled blocks of 64 primes (block 0 over every word, three words per
 // lane; later blocks over the words still open, per warp), then per-n probing.
+// One chunk of coverage words [w_begin, w_end) (32-bit words of the window
+// a.Q, 32 even n each), all in segment (row) seg, whose first n has
+// segment-relative index j_cta.  Called by every thread of the CTA; smem holds
+// the per-warp lists; shist / smax are the CTA's shared counters.
 template <int NT, int NB>
-__global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
+__device__ __forceinline__ void cover_chunk(const CoverArgs& a, uint32_t seg, uint64_t w_begin, uint64_t w_end,
+                                            uint32_t j_cta, uint32_t* smem, uint32_t* shist,
+                                            unsigned long long& smax)
 {
     constexpr int NW = NT / 32;
-    extern __shared__ uint32_t smem[];                      // per warp: list C (32-bit), then words (16-bit)
-    __shared__ uint32_t shist[kBlock * NB + 1];             // bins of the unrolled blocks' primes
-    __shared__ unsigned long long smax;
-
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    // this CTA's words (32-bit words of C, 32 even n each), all in one segment
-    const uint64_t wps = 2ull * a.words_per_seg;
-    const uint32_t seg = blockIdx.x / a.chunks_per_seg;
-    const uint32_t chunk = blockIdx.x % a.chunks_per_seg;
-    const uint64_t seg_w0 = (uint64_t)seg * wps;
-    const uint64_t w_begin = seg_w0 + (uint64_t)chunk * (2ull * a.cta_words);
-    uint64_t w_end = w_begin + 2ull * a.cta_words;
-    const uint64_t n_words32 = (a.n_count + 31) / 32;
-    if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
-    if (w_end > n_words32) w_end = n_words32;
     // a warp's list holds every word it takes in block 0
     const uint32_t cap = (2 * a.cta_words + 96 * NW - 1) / (96 * NW) * 96;
     uint32_t* lc = smem + (uint32_t)warp * cap;
     uint16_t* lw = reinterpret_cast<uint16_t*>(smem + NW * cap) + (uint32_t)warp * cap;
 
+    __syncthreads();                                        // shared counters free (previous chunk)
     for (uint32_t k = threadIdx.x; k <= (uint32_t)(kBlock * NB); k += NT) shist[k] = 0;
     if (threadIdx.x == 0) smax = 0;
     __syncthreads();
@@ -372,9 +364,8 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     const uint32_t* Qc = reinterpret_cast<const uint32_t*>(a.Q) + w_begin;   // CTA-relative words
     const uint32_t D0w = ((a.H - 4) >> 1) >> 5;            // word offset of the p = 3 partner
     const uint32_t nw_cta = (uint32_t)(w_end > w_begin ? w_end - w_begin : 0);
-    const uint64_t n_left = a.n_count - 32 * w_begin;       // n from the CTA's first n to the slab end
+    const uint64_t n_left = a.n_count - 32 * w_begin;       // n from the CTA's first n to the window end
     const uint32_t n_rel_end = (uint32_t)(n_left < 32ull * nw_cta ? n_left : 32ull * nw_cta);
-    const uint32_t j_cta = (uint32_t)(32 * (w_begin - seg_w0));   // segment-relative n of the CTA's first n
 
     uint32_t nsteps = 0, n_open = 0;
     // block 0 over every word of this warp, three consecutive words per lane
@@ -483,6 +474,85 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     for (uint32_t kk = threadIdx.x; kk <= (uint32_t)(kBlock * NB); kk += NT)
         if (shist[kk]) atomicAdd(&hrow[kk], shist[kk]);
     if (threadIdx.x == 0 && smax) atomicMax(&a.maxkey[seg], smax);
+}
+
+template <int NT, int NB>
+__global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
+{
+    extern __shared__ uint32_t smem[];                      // per warp: list C (32-bit), then words (16-bit)
+    __shared__ uint32_t shist[kBlock * NB + 1];             // bins of the unrolled blocks' primes
+    __shared__ unsigned long long smax;
+    // this CTA's words, all in one segment
+    const uint64_t wps = 2ull * a.words_per_seg;
+    const uint32_t seg = blockIdx.x / a.chunks_per_seg;
+    const uint32_t chunk = blockIdx.x % a.chunks_per_seg;
+    const uint64_t seg_w0 = (uint64_t)seg * wps;
+    const uint64_t w_begin = seg_w0 + (uint64_t)chunk * (2ull * a.cta_words);
+    uint64_t w_end = w_begin + 2ull * a.cta_words;
+    const uint64_t n_words32 = (a.n_count + 31) / 32;
+    if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
+    if (w_end > n_words32) w_end = n_words32;
+    cover_chunk<NT, NB>(a, seg, w_begin, w_end, (uint32_t)(32 * (w_begin - seg_w0)), smem, shist, smax);
+}
+
+// persistent: CTAs take (range, chunk) items from the queue until it is empty;
+// row r of the histograms, keys and counts is range r
+template <int NT, int NB>
+__global__ void __launch_bounds__(NT, 4) k_cover_items(const CoverItemsArgs a)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ uint32_t shist[kBlock * NB + 1];
+    __shared__ unsigned long long smax;
+    __shared__ uint32_t s_item;
+    const uint32_t n_items = *a.n_items;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.head, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        const uint32_t ri = a.item_range[item];
+        const BatchRange r = a.ranges[ri];
+        CoverArgs c = a.base;
+        c.Q = a.Q + r.q_off;
+        c.n_count = r.n;
+        c.n_words = (r.n + 63) / 64;
+        c.has_n4 = (r.lo == 4);
+        const uint64_t w_begin = (uint64_t)a.item_chunk[item] * (2ull * c.cta_words);
+        uint64_t w_end = w_begin + 2ull * c.cta_words;
+        const uint64_t nw32 = (r.n + 31) / 32;
+        if (w_end > nw32) w_end = nw32;
+        cover_chunk<NT, NB>(c, ri, w_begin, w_end, (uint32_t)(32 * w_begin), smem, shist, smax);
+    }
+}
+
+template <int NB>
+static cudaError_t launch_items_nb(const CoverItemsArgs& a, cudaStream_t s)
+{
+    constexpr int NT = 256;
+    const uint32_t cap = (2 * a.base.cta_words + 96 * (NT / 32) - 1) / (96 * (NT / 32)) * 96;
+    const size_t smem = (size_t)(NT / 32) * cap * 6;
+    auto k = k_cover_items<NT, NB>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem)) != cudaSuccess) return e;
+    k<<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cover_items(const CoverItemsArgs& a, int KA, cudaStream_t s)
+{
+    if (2ull * a.base.cta_words > 10ull * 768) return cudaErrorInvalidValue;
+    switch (KA) {
+    case 64: return launch_items_nb<1>(a, s);
+    case 128: return launch_items_nb<2>(a, s);
+    case 192: return launch_items_nb<3>(a, s);
+    case 256: return launch_items_nb<4>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 int cover_fast_phase_primes(uint32_t K, uint64_t n_hi)

@@ -217,15 +217,82 @@ struct FinalizeArgs {
 };
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Batched mode: many ranges in one pass of persistent kernels.  Each range has
+// its own q window inside one batch buffer; the work is split into items that
+// persistent CTAs take from device queues (atomic heads).
+// ---------------------------------------------------------------------------
+struct BatchRange {
+    uint64_t lo;                // first even n
+    uint64_t n;                 // even n in the range
+    int64_t  B;                 // odd number of bit 0 of its q window
+    uint64_t nbits;             // q window bits
+    uint64_t q_off;             // 64-bit word offset of the window in the batch buffer
+};
+
+// persistent sieve over (range, tile) items; the tile part of the primes only
+struct SieveItemsArgs {
+    SieveArgs base;             // tile_bits, primes, recip, n_warp, n_primes, wheel, strikes
+    const BatchRange* ranges;
+    const uint32_t* item_range; // per item: range index
+    const uint32_t* item_tile;  // per item: tile index within the range's window
+    const uint32_t* n_items;    // device count
+    unsigned int* head;         // queue head
+    uint32_t* Q;                // batch buffer (32-bit words)
+};
+cudaError_t launch_sieve_items(const SieveItemsArgs& a, int threads, cudaStream_t s);
+
+// persistent block cover over (range, chunk) items; row r = range r
+struct CoverItemsArgs {
+    CoverArgs base;             // H, cta_words, primes, K, hist_stride, hist, maxkey, unresolved
+    const BatchRange* ranges;
+    const uint32_t* item_range;
+    const uint32_t* item_chunk;
+    const uint32_t* n_items;
+    unsigned int* head;
+    const uint64_t* Q;          // batch buffer
+};
+cudaError_t launch_cover_items(const CoverItemsArgs& a, int KA, cudaStream_t s);
+
+// large primes over the ranges groups[group] .. groups[group+1]-1
+struct LargeBatchArgs {
+    const BatchRange* ranges;
+    const uint32_t* groups;     // device: first range of each group, then the count
+    uint32_t group;
+    const uint32_t* primes;     // the large primes
+    const uint64_t* recip;
+    uint32_t n_primes;
+    uint32_t* Q;                // batch buffer (32-bit words)
+    unsigned long long* strikes;
+};
+cudaError_t launch_large_batch(const LargeBatchArgs& a, cudaStream_t s);
+
+struct ReduceBatchArgs {
+    const BatchRange* ranges;
+    const uint32_t* count;      // device: ranges in the batch
+    const uint32_t* hist;       // [range][hist_stride]
+    uint32_t hist_stride;
+    const unsigned long long* maxkey;
+    const unsigned long long* unresolved;
+    const uint32_t* primes;
+    SegRecord* records;         // [range]
+    uint64_t* rows;             // optional [range][row_stride]
+    uint32_t row_stride;
+};
+cudaError_t launch_reduce_batch(const ReduceBatchArgs& a, uint32_t grid, cudaStream_t s);
+
 // Read-only view of a context for entry points defined outside gb_api.cu.
 struct CtxView {
     int device;
     cudaStream_t stream;
     uint64_t L;                 // primes known up to L
-    uint32_t seg_len, p1, p2, cta_threads;
+    uint32_t seg_len, p1, p2, cta_threads, tile_bits, bucket_split, warp_split;
     const uint32_t* primes;     // device [2, 3, 5, ...]
+    const uint64_t* recip;      // device Barrett reciprocals
+    const uint32_t* wheel;      // device stamp tables
     bool generic_cover;
     int ka_override;
+    uint64_t large_chunk_bits;
 };
 int ctx_view(const gb_ctx* ctx, CtxView* v);
 uint64_t ctx_pi(const gb_ctx* ctx, uint64_t x);            // primes <= x (x <= L)

@@ -1,0 +1,166 @@
+// gb_sieve_tile.cuh -- the segment sieve of one shared-memory tile, shared by
+// the per-window kernel (gb_sieve.cu) and the batched kernels (gb_batch.cu).
+#pragma once
+
+#include "gb_internal.cuh"
+
+namespace gb {
+
+__device__ __forceinline__ uint32_t pmod_u32(int64_t x, uint32_t M)
+{
+    int64_t r = x % (int64_t)M;
+    return (uint32_t)(r < 0 ? r + M : r);
+}
+
+// clear bit i of the tile: word i/32 at byte offset (i >> 3) & ~3, mask
+// ~(1 << (i & 31)) as a rotate of 0xfffffffe (the funnel shift takes i mod 32)
+__device__ __forceinline__ void strike(uint32_t* sm, uint32_t i)
+{
+    atomicAnd(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sm) + ((i >> 3) & ~3u)),
+              __funnelshift_l(0xfffffffeu, 0xfffffffeu, i));
+}
+
+// one stamp table read at pattern offset a (a < period): 32 bits from bit a
+__device__ __forceinline__ uint32_t stamp_word(const uint32_t* tab, uint32_t a)
+{
+    return __funnelshift_r(tab[a >> 5], tab[(a >> 5) + 1], a & 31);
+}
+
+// One tile of a window: bits [t0, t0 + tile_bits) of the window a.B, a.nbits,
+// sieved in shared memory (sm: tile_bits / 32 words; wt: the stamp tables
+// already loaded) and stored to a.out (word t0 / 32 on).  Called by every
+// thread of the CTA; begins with a barrier, so consecutive calls may reuse sm.
+template <int NT>
+__device__ __forceinline__ void sieve_tile(const SieveArgs& a, uint64_t t0, const uint32_t* wt, uint32_t* sm)
+{
+    constexpr int NW = NT / 32;
+    const uint32_t* w1 = wt;
+    const uint32_t* w2 = w1 + kWheelW1;
+    const uint32_t* w3 = w2 + kWheelW2;
+    const uint32_t* w4 = w3 + kWheelW3;
+
+    const uint64_t rem = a.nbits - t0;
+    const uint32_t nb = rem < a.tile_bits ? (uint32_t)rem : a.tile_bits;
+    const uint32_t nw = ((nb + 63) / 64) * 2;         // whole 64-bit words
+    const int64_t b = a.B + 2 * (int64_t)t0;          // number of the tile's bit 0
+
+    __syncthreads();                                  // sm free, wt loaded
+
+    // 1. stamp of 3..43, fix-ups for numbers <= 43 and below 2
+    {
+        const int64_t x0 = (b - 1) / 2;               // b = 2 x0 + 1 (exact: b odd)
+        const uint32_t step = 32u * NT;               // pattern advance per loop trip
+        uint32_t a1 = (pmod_u32(x0, kWheelM1) + 32u * threadIdx.x) % kWheelM1;
+        uint32_t a2 = (pmod_u32(x0, kWheelM2) + 32u * threadIdx.x) % kWheelM2;
+        uint32_t a3 = (pmod_u32(x0, kWheelM3) + 32u * threadIdx.x) % kWheelM3;
+        uint32_t a4 = (pmod_u32(x0, kWheelM4) + 32u * threadIdx.x) % kWheelM4;
+        const uint32_t s1 = step % kWheelM1, s2 = step % kWheelM2, s3 = step % kWheelM3, s4 = step % kWheelM4;
+        for (uint32_t w = threadIdx.x; w < nw; w += NT) {
+            uint32_t v = stamp_word(w1, a1) & stamp_word(w2, a2) & stamp_word(w3, a3) & stamp_word(w4, a4);
+            const int64_t v0 = b + 64 * (int64_t)w;   // number of this word's bit 0
+            if (v0 <= 43) {
+                // the stamped primes themselves are prime; numbers < 2 are not
+                for (uint32_t k = 0; k < 32; ++k) {
+                    const int64_t num = v0 + 2 * (int64_t)k;
+                    if (num < 2) {
+                        v &= ~(1u << k);
+                    } else if (num <= 43) {
+                        const bool pr = num == 3 || num == 5 || num == 7 || num == 11 || num == 13 ||
+                                        num == 17 || num == 19 || num == 23 || num == 29 || num == 31 ||
+                                        num == 37 || num == 41 || num == 43;
+                        if (pr) v |= 1u << k;
+                    }
+                }
+            }
+            sm[w] = v;
+            a1 += s1; if (a1 >= kWheelM1) a1 -= kWheelM1;
+            a2 += s2; if (a2 >= kWheelM2) a2 -= kWheelM2;
+            a3 += s3; if (a3 >= kWheelM3) a3 -= kWheelM3;
+            a4 += s4; if (a4 >= kWheelM4) a4 -= kWheelM4;
+        }
+    }
+    __syncthreads();
+
+    // 2. strikes of the primes 47 <= p with p^2 <= the tile's last number
+    const int64_t last = b + 2 * (int64_t)(nb - 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long nstrike = 0;
+    // 2a. small primes, one warp each: warp w takes the primes w, w + NW, ...;
+    // 32 of them at a time, each lane computing one prime's first index
+    for (uint32_t k0 = warp; k0 < a.n_warp; k0 += 32 * NW) {
+        const uint32_t k = k0 + (uint32_t)lane * NW;
+        uint32_t p = 0, i0 = nb;
+        if (k < a.n_warp) {
+            p = a.primes[k];
+            const uint64_t pp = (uint64_t)p * p;
+            if ((int64_t)pp <= last) {
+                i0 = first_odd_multiple(b, p, a.recip[k]);
+                if ((int64_t)pp > b) {
+                    const uint32_t isq = (uint32_t)(((int64_t)pp - b) >> 1);
+                    if (isq > i0) i0 = isq;              // same residue class mod p
+                }
+            }
+        }
+        if (a.strikes && i0 < nb) nstrike += (nb - 1 - i0) / p + 1;
+        unsigned pending = __ballot_sync(0xffffffffu, i0 < nb);
+        while (pending) {
+            const int src = __ffs(pending) - 1;
+            pending &= pending - 1;
+            const uint32_t q = __shfl_sync(0xffffffffu, p, src);
+            const uint32_t j0 = __shfl_sync(0xffffffffu, i0, src);
+            const uint32_t step = 32u * q;
+            uint32_t i = j0 + (uint32_t)lane * q;
+            // step <= 2^15 and i < 2^20: no wrap below
+            for (; i + 3 * step < nb; i += 4 * step) {
+                strike(sm, i);
+                strike(sm, i + step);
+                strike(sm, i + 2 * step);
+                strike(sm, i + 3 * step);
+            }
+            for (; i < nb; i += step) strike(sm, i);
+        }
+    }
+    // 2b. larger primes, one thread each
+    for (uint32_t k = a.n_warp + threadIdx.x; k < a.n_primes; k += NT) {
+        const uint32_t p = a.primes[k];
+        const uint64_t pp = (uint64_t)p * p;
+        if ((int64_t)pp > last) break;
+        uint32_t i = first_odd_multiple(b, p, a.recip[k]);
+        if ((int64_t)pp > b) {
+            uint32_t isq = (uint32_t)(((int64_t)pp - b) >> 1);
+            if (isq > i) i = isq;
+        }
+        if (a.strikes && i < nb) nstrike += (nb - 1 - i) / p + 1;
+        // i < 2^20 and p < 3.1e9 (p^2 < 2^63): i + p cannot wrap
+        if (p < (1u << 20)) {
+            for (; i + p < nb; i += 2 * p) {
+                strike(sm, i);
+                strike(sm, i + p);
+            }
+        }
+        for (; i < nb; i += p) strike(sm, i);
+    }
+    if (a.strikes) {
+        for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);
+        if (lane == 0 && nstrike) atomicAdd(a.strikes, nstrike);
+    }
+    __syncthreads();
+
+    // 3. clear bits past the window end, store, count
+    uint32_t cnt = 0;
+    uint32_t* dst = a.out ? a.out + t0 / 32 : nullptr;
+    for (uint32_t w = threadIdx.x; w < nw; w += NT) {
+        uint32_t v = sm[w];
+        const uint32_t bit0 = 32u * w;
+        if (bit0 >= nb) v = 0;
+        else if (nb - bit0 < 32) v &= (1u << (nb - bit0)) - 1u;
+        cnt += __popc(v);
+        if (dst) dst[w] = v;
+    }
+    if (a.popcount) {
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0 && cnt) atomicAdd(a.popcount, (unsigned long long)cnt);
+    }
+}
+
+}  // namespace gb

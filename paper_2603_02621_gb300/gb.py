@@ -59,6 +59,8 @@ SIGNATURES = {
     "gb_prime_pi": (c_int, [c_void_p, c_uint64, POINTER(c_uint64)]),
     "gb_verify_range": (c_int, [c_void_p, c_uint64, c_uint64, c_uint32, POINTER(gb_range_result)]),
     "gb_verify_range_noalloc": (c_int, [c_void_p, c_uint64, c_uint64, c_uint32, POINTER(gb_range_result)]),
+    "gb_verify_batch": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), c_uint32, c_uint32,
+                                c_void_p, c_void_p, c_uint32]),
     "gb_profile_enable": (c_int, [c_void_p, c_int]),
     "gb_profile_read": (c_int, [c_void_p, POINTER(ctypes.c_double), POINTER(c_uint64), POINTER(c_uint64)]),
     "gb_profile_work": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64)]),
@@ -235,6 +237,40 @@ def gb_profile_work(ctx: int) -> dict:
     return dict(sieve_strikes=a.value, cover_iterations=b.value)
 
 
+def gb_verify_batch(ctx: int, ranges, P: int = 0, *, hist_stride: int = 0, results=None, hist=None,
+                    allow_erange: bool = False) -> dict:
+    """Verify many ranges [(lo, hi), ...] in one batched pass.  Returns a dict
+    with 'records' (list of per-range dicts) and 'hist' (np.uint64[count,
+    hist_stride]) when hist_stride > 0.  results / hist may be given as device
+    buffers (torch CUDA tensors of gb_segment_result rows / uint64), in which
+    case they are filled in place and not copied back."""
+    lib = load()
+    count = len(ranges)
+    lo = (c_uint64 * count)(*[int(a) for a, _ in ranges])
+    hi = (c_uint64 * count)(*[int(b) for _, b in ranges])
+    recs = None
+    if results is None:
+        recs = (gb_segment_result * count)()
+        res_ptr = ctypes.addressof(recs)
+    else:
+        res_ptr = _ptr(results)
+    rows = None
+    if hist is None and hist_stride:
+        rows = np.zeros((count, hist_stride), dtype=np.uint64)
+        hist_ptr = int(rows.ctypes.data)
+    else:
+        hist_ptr = _ptr(hist)
+    rc = _check(lib.gb_verify_batch(ctx, lo, hi, count, P, res_ptr, hist_ptr, hist_stride), "gb_verify_batch",
+                allow=(GB_ERANGE,) if allow_erange else ())
+    out = {"rc": rc}
+    if recs is not None:
+        out["records"] = [dict(lo=r.lo, hi=r.hi, n_checked=r.n_checked, unresolved=r.unresolved,
+                               max_pmin=r.max_pmin, max_pmin_n=r.max_pmin_n, hist_len=r.hist_len) for r in recs]
+    if rows is not None:
+        out["hist"] = rows
+    return out
+
+
 def gb_bitset_bytes(N: int) -> int:
     return int(load().gb_bitset_bytes(N))
 
@@ -284,3 +320,6 @@ class Context:
 
     def verify_range_noalloc(self, lo, hi, P=0, **kw):
         return gb_verify_range_noalloc(self.handle, lo, hi, P, **kw)
+
+    def verify_batch(self, ranges, P=0, **kw):
+        return gb_verify_batch(self.handle, ranges, P, **kw)

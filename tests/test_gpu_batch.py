@@ -1,0 +1,132 @@
+"""Batched mode (gb_verify_batch): many ranges of uneven length and offset in
+one pass, compared range by range with the CPU oracle and with the plain
+gb_verify_range path.  Integer outputs, bit-exact."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+P1 = 1 << 15
+P2 = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def gbm():
+    from paper_2603_02621_gb300 import gb
+    gb.load()
+    assert torch.cuda.is_available()
+    return gb
+
+
+@pytest.fixture(scope="module")
+def ctx(gbm):
+    # base primes to 2^31: windows up to 4.6e18
+    with gbm.Context(device=0, base_limit=1 << 31, seg_len=1 << 20, p1=P1, p2=P2) as g:
+        yield g
+
+
+def _check_vs_oracle(oracle, ranges, out, stride):
+    for i, (lo, hi) in enumerate(ranges):
+        n = (hi - lo) // 2
+        summ, hist = oracle.verify_segments(lo, hi, n, P2, stride)
+        r = out["records"][i]
+        assert (r["lo"], r["hi"], r["n_checked"]) == (lo, hi, n), (lo, hi)
+        assert r["unresolved"] == int(summ[0, 1]), (lo, hi)
+        assert (r["max_pmin"], r["max_pmin_n"]) == (int(summ[0, 2]), int(summ[0, 3])), (lo, hi)
+        if stride:
+            np.testing.assert_array_equal(out["hist"][i], hist[0], err_msg=f"{lo} {hi}")
+            nz = np.nonzero(hist[0])[0]
+            assert r["hist_len"] == (int(nz[-1]) + 1 if len(nz) else 0)
+
+
+def _mixed_ranges():
+    from paper_2603_02621_gb300.workloads import batched_ranges
+    fixed = [
+        (4, 6),                           # n = 4 alone (p_min 2)
+        (4, 4 + 2 * 5003),                # from the start, ragged
+        (6, 8),
+        (10**6, 10**6 + 2),               # one n
+        (10**9, 10**9 + 2 * 70001),       # several block-cover chunks
+        (2 * 10**10, 2 * 10**10 + 2 * 7680 * 32),   # exactly one chunk of words
+        (3 * 10**11 + 2, 3 * 10**11 + 2 + 2 * 300007),  # primes above a tile (bucket path)
+    ]
+    rnd = batched_ranges(count=40, seed=11, log2_min=3, log2_max=17, start_min=10**6, start_max=10**12)
+    return fixed + rnd
+
+
+def test_batch_vs_oracle(ctx, oracle):
+    ranges = _mixed_ranges()
+    stride = len(oracle.primes_upto(P1))
+    out = ctx.verify_batch(ranges, hist_stride=stride)
+    _check_vs_oracle(oracle, ranges, out, stride)
+
+
+def test_batch_matches_verify_range(ctx):
+    from paper_2603_02621_gb300.workloads import batched_ranges
+    ranges = batched_ranges(count=24, seed=5, log2_min=10, log2_max=22, start_min=10**9, start_max=10**15)
+    ranges += [(10**15, 10**15 + 2 * (1 << 22)), (4 * 10**18, 4 * 10**18 + 2 * 100003)]
+    stride = 4096
+    out = ctx.verify_batch(ranges, hist_stride=stride)
+    for i, (lo, hi) in enumerate(ranges):
+        ref = ctx.verify_range(lo, hi, hist_cap=stride)
+        r = out["records"][i]
+        for k in ("n_checked", "unresolved", "max_pmin", "max_pmin_n", "hist_len"):
+            assert r[k] == ref[k], (lo, hi, k)
+        np.testing.assert_array_equal(out["hist"][i], ref["hist"], err_msg=f"{lo} {hi}")
+
+
+def test_batch_device_outputs(ctx, oracle):
+    ranges = _mixed_ranges()[:20]
+    stride = 512
+    host = ctx.verify_batch(ranges, hist_stride=stride)
+    res = torch.zeros((len(ranges), 48), dtype=torch.uint8, device="cuda")
+    rows = torch.zeros((len(ranges), stride), dtype=torch.int64, device="cuda")
+    ctx.verify_batch(ranges, hist_stride=stride, results=res, hist=rows)
+    raw = res.cpu().numpy()
+    u64 = raw[:, :40].copy().view(np.uint64)
+    u32 = raw[:, 40:].copy().view(np.uint32)
+    for i, r in enumerate(host["records"]):
+        assert [int(x) for x in u64[i]] == [r["lo"], r["hi"], r["n_checked"], r["unresolved"], r["max_pmin_n"]]
+        assert [int(x) for x in u32[i]] == [r["max_pmin"], r["hist_len"]]
+    np.testing.assert_array_equal(rows.cpu().numpy().view(np.uint64), host["hist"])
+
+
+def test_batch_small_P_redo(ctx, oracle):
+    # P = 313 (64 odd primes): many n stay open after the batched pass and are
+    # redone by the plain path with its retry bound
+    ranges = [(10**11, 10**11 + 2 * 40001), (10**12 + 2, 10**12 + 2 + 2 * 20011), (10**6, 10**6 + 2 * 999)]
+    out = ctx.verify_batch(ranges, 313, hist_stride=256)
+    _check_vs_oracle(oracle, ranges, out, 256)
+    for i, (lo, hi) in enumerate(ranges):
+        ref = ctx.verify_range(lo, hi, 313, hist_cap=256)
+        assert out["records"][i]["max_pmin"] == ref["max_pmin"]
+
+
+def test_batch_rejects_bad_input(ctx, gbm):
+    assert ctx.verify_batch([])["rc"] == gbm.GB_OK
+    with pytest.raises(RuntimeError):
+        ctx.verify_batch([(10**6 + 1, 10**6 + 11)])
+    with pytest.raises(RuntimeError):
+        ctx.verify_batch([(10**6, 10**6)])
+    with pytest.raises(RuntimeError):
+        ctx.verify_batch([(10**6, 10**6 + 100)], 17)     # fewer than 64 odd primes
+    out = ctx.verify_batch([(10**9, 10**9 + 2 * 5000)], hist_stride=3, allow_erange=True)
+    assert out["rc"] == gbm.GB_ERANGE and out["records"][0]["hist_len"] > 3
+
+
+def test_batch_4096_ranges_sampled(ctx, oracle):
+    """The 4096-range workload (lengths log-uniform 2^10..2^26 even n, starts
+    uniform in [1e9, 1e15]): invariants on every range, the oracle in full on
+    a seeded sample of the shorter ranges."""
+    from paper_2603_02621_gb300.workloads import batched_ranges, sample_indices
+    ranges = batched_ranges(count=4096, seed=1)
+    out = ctx.verify_batch(ranges)
+    for (lo, hi), r in zip(ranges, out["records"]):
+        assert (r["lo"], r["hi"], r["n_checked"], r["unresolved"]) == (lo, hi, (hi - lo) // 2, 0)
+        assert lo <= r["max_pmin_n"] < hi
+        assert oracle.mr_isprime(r["max_pmin"]) and oracle.mr_isprime(r["max_pmin_n"] - r["max_pmin"])
+    short = [i for i, (lo, hi) in enumerate(ranges) if (hi - lo) // 2 <= (1 << 18)]
+    pick = [short[k] for k in sample_indices(len(short), 12, seed=3)]
+    _check_vs_oracle(oracle, [ranges[i] for i in pick], {"records": [out["records"][i] for i in pick]}, 0)
