@@ -1,13 +1,22 @@
-"""Benchmark: exhaustive Goldbach verification of [4, 10^10] on the GPU.
+"""Benchmark of the Goldbach verifier on the GPU (one JSON line, rank 0).
 
-One step = one gb_verify_range call over every even n of the workload:
-segment sieve of the q window, the loop-inverted cover with P1 = 2^15, the GPU
-retry pass to P2 = 2^20, per-segment reductions (GoldbachGPU, arXiv
-2603.02621, Sec. 2.3; Table 4 reports the same workload's exhaustive run).
+Modes (--mode), each a workload of GoldbachGPU (arXiv 2603.02621):
 
-Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): rank r verifies its own
-range [4 + r*10^10, 4 + (r+1)*10^10 - 2) -- independent work, no collective on
-the data path (weak scaling); the timing is the max over ranks.
+* plain (default): exhaustive verification of every even n in [4, 10^10]
+  (Table 4's workload): one step = one gb_verify_range call: segment sieve of
+  the q window, the loop-inverted cover with P1 = 2^15, the GPU retry pass to
+  P2 = 2^20, per-segment reductions (Sec. 2.3);
+* exhaustive-1e12: [4, 10^12] (Table 5's range), segments of 2^27 even n,
+  base primes to 2^31;
+* window-4e18: the 10^11-wide window [4e18 - 10^11, 4e18), segments of 2^27;
+* batched: 4096 ranges of uneven length (log-uniform 2^10..2^26 even n) and
+  offset (uniform in [10^9, 10^15]) in one gb_verify_batch call after the
+  autotuner has picked tile, split, P1 and cover prefix; the plain per-range
+  launch loop over the same ranges, with the same outputs, is timed beside it.
+
+Multi-GPU (torchrun): each rank verifies its own shard (plain family: the next
+range of the same width; batched: its own 4096 ranges) -- independent work, no
+collective on the data path (weak scaling); the timing is the max over ranks.
 
 --impl reference times the CPU oracle (oracle/) on a bounded sample of the
 same workload, on the host cores.
@@ -29,23 +38,48 @@ sys.path.insert(0, ROOT)
 
 METRIC = "even integers verified/sec"
 UNIT = "even n/s"
-SEG = 1 << 24
 P1, P2 = 1 << 15, 1 << 20
-SPAN = 10**10                       # even n per rank: SPAN/2 - 1
+HL = 3512                           # pi(2^15): histogram row length
 PAPER_NPS = 4999999999 / 23.547     # Table 4: [4, 1e10] in 23,547 ms on an RTX 3070
+PAPER_CONTEXT = "RTX 3070, Table 4: [4, 1e10] in 23,547 ms = 2.12e8 n/s"
+
+# plain-family workloads: (first range, shift per rank, segment length, base primes)
+PLAIN_MODES = {
+    "plain": dict(lo=4, hi=10**10 + 2, shift=10**10, seg=1 << 24, base=None,
+                  workload="exhaustive Goldbach verification of every even n in [4, 1e10] per GPU"),
+    "exhaustive-1e12": dict(lo=4, hi=10**12 + 2, shift=10**12, seg=1 << 27, base=1 << 31,
+                            workload="exhaustive Goldbach verification of every even n in [4, 1e12] per GPU"),
+    "window-4e18": dict(lo=4 * 10**18 - 10**11, hi=4 * 10**18, shift=-10**11, seg=1 << 27, base=1 << 31,
+                        workload="Goldbach verification of the window [4e18 - 1e11, 4e18) per GPU"),
+}
 
 
-def rank_range(rank: int):
-    lo = 4 + rank * SPAN
-    return lo, lo + SPAN - 2        # [4, 1e10 + 2) for rank 0: 4,999,999,999 even n
+def rank_range(mode: str, rank: int):
+    m = PLAIN_MODES[mode]
+    return m["lo"] + rank * m["shift"], m["hi"] + rank * m["shift"]
 
 
-def workload_desc(world: int):
-    return {"workload": "exhaustive Goldbach verification of every even n in [4, 1e10] per GPU",
-            "ranges": [list(rank_range(r)) for r in range(world)],
-            "seg_len": SEG, "base_primes_to": "isqrt(hi)+ (>= 1e5)", "p1": P1, "p2": P2,
-            "outputs": "per-segment p_min histogram (3512 entries), max p_min with n, unresolved",
-            "l2": "q window 625 MB per GPU > 126 MB L2; no flush needed"}
+def base_for(mode: str, hi: int) -> int:
+    b = PLAIN_MODES[mode]["base"] if mode in PLAIN_MODES else None
+    return b or max(10**5, math.isqrt(hi + 4096) + 1)
+
+
+def workload_desc(mode: str, world: int):
+    if mode == "batched":
+        return {"workload": "4096 ranges per GPU, lengths log-uniform 2^10..2^26 even n, starts uniform "
+                            "in [1e9, 1e15] (splitmix64 seed 1 + rank), one gb_verify_batch call",
+                "ranges": 4096, "seeds": [1 + r for r in range(world)], "base_primes_to": 32 * 10**6,
+                "p2": P2, "outputs": f"per-range record and p_min histogram row ({HL} entries)",
+                "tuning": "gb_autotune on the same batch before timing",
+                "l2": "batch q buffer ~3.1 GB > 126 MB L2; no flush needed"}
+    m = PLAIN_MODES[mode]
+    lo, hi = rank_range(mode, 0)
+    n = (hi - lo) // 2
+    return {"workload": m["workload"], "ranges": [list(rank_range(mode, r)) for r in range(world)],
+            "seg_len": m["seg"], "base_primes_to": base_for(mode, hi) if m["base"] else "isqrt(hi)+ (>= 1e5)",
+            "p1": P1, "p2": P2,
+            "outputs": f"per-segment p_min histogram ({HL} entries), max p_min with n, unresolved",
+            "l2": f"q window {n / 8 / 1e6:.0f} MB per GPU > 126 MB L2; no flush needed"}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -131,38 +165,53 @@ def barrier(world: int, backend_ready: bool):
 
 
 # ----------------------------------------------------------------------------- cpu baseline
-def cpu_baseline(min_seconds: float = 12.0, seed: int = 11):
-    """The oracle, as it stands, on a bounded sample of the workload's segments."""
-    from oracle import oracle
+def sample_units(mode: str, seed: int = 11):
+    """The workload cut into independent units (lo, hi) the oracle can verify
+    one by one, in a seeded random order: segments for the plain family,
+    ranges for the batched mode."""
     from paper_2603_02621_gb300 import workloads
-    lo, hi = rank_range(0)
-    nseg = ((hi - lo) // 2 + SEG - 1) // SEG
-    threads = oracle.default_threads()
-    order = workloads.sample_indices(nseg, nseg, seed=seed)
+    if mode == "batched":
+        units = workloads.batched_ranges(count=4096, seed=1)
+    else:
+        lo, hi = rank_range(mode, 0)
+        seg = PLAIN_MODES[mode]["seg"]
+        units = [(a, min(a + 2 * seg, hi)) for a in range(lo, hi, 2 * seg)]
     rng = workloads.SplitMix64(seed)
-    for i in range(len(order) - 1, 0, -1):          # seeded shuffle of the segment order
+    order = list(range(len(units)))
+    for i in range(len(order) - 1, 0, -1):          # seeded shuffle
         j = rng.below(i + 1)
         order[i], order[j] = order[j], order[i]
-    hl = 3512
-    import concurrent.futures as cf
+    return [units[i] for i in order]
 
-    def one(k):
-        # one sampled segment, verified by the oracle in one thread
-        a = lo + 2 * k * SEG
-        b = min(a + 2 * SEG, hi)
-        s, _ = oracle.verify_segments(a, b, SEG, P2, hl, threads=1)
+
+def cpu_baseline(mode: str = "plain", min_seconds: float = 12.0, seed: int = 11):
+    """The oracle, as it stands, on a bounded sample of the workload's units
+    (one unit per host thread at a time)."""
+    from oracle import oracle
+    import concurrent.futures as cf
+    threads = oracle.default_threads()
+    units = sample_units(mode, seed)
+    if mode != "plain":
+        oracle.primes_upto(3)                           # (cached small primes are built on first use)
+        lo_max = max(b for _, b in units)
+        oracle.verify_segments(lo_max - 4, lo_max, 2, P2, 8, threads=1)   # warm the prime cache untimed
+
+    def one(u):
+        a, b = u
+        n = (b - a) // 2
+        s, _ = oracle.verify_segments(a, b, n, P2, HL, threads=1)
         return int(s[:, 0].sum())
 
-    done_n, t0, used = 0, time.perf_counter(), []
+    done_n, t0, used = 0, time.perf_counter(), 0
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        while time.perf_counter() - t0 < min_seconds and len(used) < nseg:
-            batch = order[len(used):len(used) + threads]
+        while time.perf_counter() - t0 < min_seconds and used < len(units):
+            batch = units[used:used + threads]
             done_n += sum(ex.map(one, batch))
-            used += batch
+            used += len(batch)
     dt = time.perf_counter() - t0
+    kind = "ranges of the 4096-range batch" if mode == "batched" else "segments of " + mode
     return {"value": done_n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{len(used)} seeded segments of 2^24 even n from [4, 1e10] "
-                      f"({done_n} n, {dt:.1f} s wall, P = 2^20)",
+            "sample": f"{used} seeded {kind} ({done_n} n, {dt:.1f} s wall, P = 2^20)",
             "seconds": dt}
 
 
@@ -171,18 +220,20 @@ def run_reference(args, world, rank):
         return 0
     per_step = max(4.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_baseline(min_seconds=1.0)
+        cpu_baseline(args.mode, min_seconds=1.0)
     vals = []
     last = None
     for _ in range(args.steps):
-        last = cpu_baseline(min_seconds=per_step)
+        last = cpu_baseline(args.mode, min_seconds=per_step)
         vals.append(last["value"])
     value = statistics.mean(vals)
+    n_step = workload_n(args.mode)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * (SPAN // 2 - 1) / value,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_NPS,
-            "dtype": "u64", "data": "synthetic", "config": workload_desc(1),
+            "ms_per_step": 1000.0 * n_step / value,
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / PAPER_NPS if args.mode == "plain" else None,
+            "dtype": "u64", "data": "synthetic", "mode": args.mode, "config": workload_desc(args.mode, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -190,13 +241,149 @@ def run_reference(args, world, rank):
     return 0
 
 
+def workload_n(mode: str, rank: int = 0) -> int:
+    if mode == "batched":
+        from paper_2603_02621_gb300 import workloads
+        return sum((b - a) // 2 for a, b in workloads.batched_ranges(count=4096, seed=1 + rank))
+    lo, hi = rank_range(mode, rank)
+    return (hi - lo) // 2
+
+
+# ----------------------------------------------------------------------------- workloads on the GPU
+class PlainWork:
+    """One gb_verify_range call over the rank's range per step."""
+
+    def __init__(self, gb, torch, mode, rank, local, stream):
+        self.gb = gb
+        self.lo, self.hi = rank_range(mode, rank)
+        self.seg = PLAIN_MODES[mode]["seg"]
+        self.ctx = gb.Context(device=local, base_limit=base_for(mode, self.hi), seg_len=self.seg,
+                              p1=P1, p2=P2, stream=stream.cuda_stream)
+        self.nseg = ((self.hi - self.lo) // 2 + self.seg - 1) // self.seg
+        self.n = (self.hi - self.lo) // 2
+        # device-resident outputs for the device-timed value, pinned host ones for e2e
+        self.d_rows = torch.zeros((self.nseg, HL), dtype=torch.int64, device="cuda")
+        self.d_segs = torch.zeros((self.nseg, 6), dtype=torch.int64, device="cuda")    # 48-byte records
+        self.h_rows = torch.zeros((self.nseg, HL), dtype=torch.int64).pin_memory()
+        self.h_segs = torch.zeros((self.nseg, 6), dtype=torch.int64).pin_memory()
+        self.h_hist = torch.zeros(HL, dtype=torch.int64).pin_memory()
+        self.h2d = 0
+        self.d2h = 32 + self.nseg * 48 + self.nseg * HL * 8 + HL * 8
+        self.last = None
+
+    def _call(self, rows, segs, hist):
+        gb = self.gb
+        r = gb.gb_range_result()
+        r.seg_hist = ctypes_ptr(rows)
+        r.seg_hist_stride = HL
+        r.seg_cap = self.nseg
+        r.segs = ctypes_segs(segs)
+        if hist is not None:
+            r.hist = ctypes_ptr(hist)
+            r.hist_cap = HL
+        rc = gb.load().gb_verify_range(self.ctx.handle, self.lo, self.hi, 0, gb.ctypes.byref(r))
+        if rc:
+            raise gb.GbError(rc, "gb_verify_range", gb.gb_last_error())
+        self.last = r
+        return r
+
+    def step_device(self):
+        return self._call(self.d_rows, self.d_segs, None)
+
+    def step_host(self):
+        return self._call(self.h_rows, self.h_segs, self.h_hist)
+
+    def check(self):
+        r = self.last
+        return {"unresolved": int(r.unresolved), "max_pmin": int(r.max_pmin),
+                "max_pmin_n": int(r.max_pmin_n), "n_checked": int(r.n_checked)}
+
+    def extra(self, args):
+        return {}
+
+
+class BatchWork:
+    """One gb_verify_batch call over the rank's 4096 ranges per step."""
+
+    def __init__(self, gb, torch, mode, rank, local, stream):
+        from paper_2603_02621_gb300 import workloads
+        self.gb, self.torch = gb, torch
+        self.ranges = workloads.batched_ranges(count=4096, seed=1 + rank)
+        self.count = len(self.ranges)
+        self.n = sum((b - a) // 2 for a, b in self.ranges)
+        self.ctx = gb.Context(device=local, base_limit=32 * 10**6, seg_len=1 << 24, p1=P1, p2=P2,
+                              stream=stream.cuda_stream)
+        self.lo = (gb.c_uint64 * self.count)(*[a for a, _ in self.ranges])
+        self.hi = (gb.c_uint64 * self.count)(*[b for _, b in self.ranges])
+        self.d_res = torch.zeros((self.count, 6), dtype=torch.int64, device="cuda")
+        self.d_rows = torch.zeros((self.count, HL), dtype=torch.int64, device="cuda")
+        self.h_res = torch.zeros((self.count, 6), dtype=torch.int64).pin_memory()
+        self.h_rows = torch.zeros((self.count, HL), dtype=torch.int64).pin_memory()
+        self.h2d = 0                       # the range list is host memory the call reads (count x 16 B)
+        self.d2h = self.count * 48 + self.count * HL * 8
+        self.tuned, self.tune_ms = self.ctx.autotune(self.ranges, gb.GB_TUNE_BATCH, reps=1)
+
+    def _call(self, res, rows):
+        gb = self.gb
+        rc = gb.load().gb_verify_batch(self.ctx.handle, self.lo, self.hi, self.count, 0,
+                                       res.data_ptr(), rows.data_ptr(), HL)
+        if rc:
+            raise gb.GbError(rc, "gb_verify_batch", gb.gb_last_error())
+
+    def step_device(self):
+        self._call(self.d_res, self.d_rows)
+
+    def step_host(self):
+        self._call(self.h_res, self.h_rows)
+
+    def check(self):
+        import numpy as np
+        raw = self.h_res.numpy().view(np.uint64)
+        unres = int(raw[:, 3].sum())
+        mp = (raw[:, 5] & 0xffffffff).astype(np.int64)
+        k = int(np.argmax(mp))
+        return {"unresolved": unres, "max_pmin": int(mp[k]), "max_pmin_n": int(raw[k, 4]),
+                "n_checked": int(raw[:, 2].sum())}
+
+    def extra(self, args):
+        """The plain per-range launch loop over the same ranges, same outputs
+        (per-range totals and histogram row, device-resident), timed once after
+        one warm-up pass; and the batch without its CUDA graph."""
+        gb, torch = self.gb, self.torch
+        d_hist = torch.zeros((self.count, HL), dtype=torch.int64, device="cuda")
+        lib = gb.load()
+
+        def loop():
+            for i, (a, b) in enumerate(self.ranges):
+                r = gb.gb_range_result()
+                r.hist = ctypes_ptr(d_hist[i])
+                r.hist_cap = HL
+                rc = lib.gb_verify_range(self.ctx.handle, a, b, 0, gb.ctypes.byref(r))
+                if rc:
+                    raise gb.GbError(rc, "gb_verify_range", gb.gb_last_error())
+
+        loop()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loop()
+        torch.cuda.synchronize()
+        loop_s = time.perf_counter() - t0
+        same = bool(torch.equal(d_hist, self.d_rows))
+        return {"plain_loop": {"value": self.n / loop_s, "unit": UNIT, "ms": 1000.0 * loop_s,
+                               "launch": "gb_verify_range per range, same per-range histograms",
+                               "same_histograms": same},
+                "autotuned": {k: self.tuned[k] for k in ("tile_bits", "bucket_split", "p1", "cover_prefix")},
+                "autotune_best_ms": self.tune_ms}
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="plain", choices=sorted(PLAIN_MODES) + ["batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lo", type=int, default=None, help="custom range start (profiling of smaller cases)")
     ap.add_argument("--hi", type=int, default=None, help="custom range end")
@@ -205,7 +392,6 @@ def main():
     if args.impl == "reference":
         return run_reference(args, world, rank)
 
-    import numpy as np
     import torch
     from paper_2603_02621_gb300 import gb
 
@@ -216,51 +402,16 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         backend_ready = True
     stream = torch.cuda.current_stream()
-    lo, hi = rank_range(rank)
-    if args.lo is not None and args.hi is not None:
-        lo, hi = args.lo, args.hi
-    base = max(10**5, math.isqrt(hi + 4096) + 1)
-    ctx = gb.Context(device=local, base_limit=base, seg_len=SEG, p1=P1, p2=P2,
-                     stream=stream.cuda_stream)
-    nseg = ((hi - lo) // 2 + SEG - 1) // SEG
-    HL = 3512                                       # pi(2^15): per-segment row length
-    n_per_step = (hi - lo) // 2
-
-    # device-resident outputs for the device-timed value
-    d_rows = torch.zeros((nseg, HL), dtype=torch.int64, device="cuda")
-    d_segs = torch.zeros((nseg, 6), dtype=torch.int64, device="cuda")      # 48-byte records
-
-    def step_device():
-        r = gb.gb_range_result()
-        r.seg_hist = ctypes_ptr(d_rows)
-        r.seg_hist_stride = HL
-        r.seg_cap = nseg
-        r.segs = ctypes_segs(d_segs)
-        rc = gb.load().gb_verify_range(ctx.handle, lo, hi, 0, gb.ctypes.byref(r))
-        if rc:
-            raise gb.GbError(rc, "gb_verify_range", gb.gb_last_error())
-        return r
-
-    # pinned host outputs for the end-to-end number
-    h_rows = torch.zeros((nseg, HL), dtype=torch.int64).pin_memory()
-    h_segs = torch.zeros((nseg, 6), dtype=torch.int64).pin_memory()
-    h_hist = torch.zeros(HL, dtype=torch.int64).pin_memory()
-
-    def step_host():
-        r = gb.gb_range_result()
-        r.seg_hist = ctypes_ptr(h_rows)
-        r.seg_hist_stride = HL
-        r.seg_cap = nseg
-        r.segs = ctypes_segs(h_segs)
-        r.hist = ctypes_ptr(h_hist)
-        r.hist_cap = HL
-        rc = gb.load().gb_verify_range(ctx.handle, lo, hi, 0, gb.ctypes.byref(r))
-        if rc:
-            raise gb.GbError(rc, "gb_verify_range", gb.gb_last_error())
-        return r
+    if args.mode == "batched":
+        work = BatchWork(gb, torch, args.mode, rank, local, stream)
+    else:
+        if args.lo is not None and args.hi is not None:
+            PLAIN_MODES[args.mode].update(lo=args.lo, hi=args.hi, shift=args.hi - args.lo)
+        work = PlainWork(gb, torch, args.mode, rank, local, stream)
+    ctx = work.ctx
 
     for _ in range(args.warmup):
-        step_device()
+        work.step_device()
     torch.cuda.synchronize()
 
     # ---- device-timed region (value), per-kernel events, clocks
@@ -272,16 +423,15 @@ def main():
     time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    last = None
     for _ in range(args.steps):
-        last = step_device()
+        work.step_device()
     ev1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
     barrier(world, backend_ready)
     dev_ms = ev0.elapsed_time(ev1)
     prof = gb.gb_profile_read(ctx.handle)
-    work = gb.gb_profile_work(ctx.handle)
+    wk = gb.gb_profile_work(ctx.handle)
+    launches = gb.gb_profile_kernels(ctx.handle)
     gb.gb_profile_enable(ctx.handle, False)
     max_ms = reduce_max(dev_ms, world, backend_ready)
 
@@ -290,15 +440,15 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step_host()
+        work.step_host()
     torch.cuda.synchronize()
     e2e_ms = 1000.0 * (time.perf_counter() - t0)
+    clk = clocks.stop()
     e2e_ms = reduce_max(e2e_ms, world, backend_ready)
 
-    total_n = n_per_step * args.steps * world
+    total_n = work.n * args.steps * world
     value = total_n / (max_ms / 1000.0)
     e2e_value = total_n / (e2e_ms / 1000.0)
-    d2h = 32 + nseg * 48 + nseg * HL * 8 + HL * 8
 
     # ---- roofline of the dominant kernel (per-launch averages over the timed region)
     peaks, peak_src = load_peaks()
@@ -308,28 +458,26 @@ def main():
     # and clock: 152 SMs x 64 ALU lanes per cycle (16 per scheduler: half the
     # issue rate, measured by a shift/or loop) x the maximum SM clock.
     alu_peak = 152 * 64 * sm_max * 1e6 / 1e12            # T ALU lane-ops/s
+    # DRAM bytes per unit measured by ncu on [4, 2^32] (plain workload's kernels)
+    ncu_traffic = {"cover": 0.1269, "sieve": 0.09657} if args.mode == "plain" else {}
     per = {}
     for kern in ("sieve", "cover"):
         kp = prof[kern]
-        launches = max(1, kp["launches"])
-        ms = kp["ms"] / launches
+        nl = max(1, kp["launches"])
+        ms = kp["ms"] / nl
         if kern == "cover":
             # minimal ALU work: 2 ops per (32-bit coverage word, prime) step,
             # the funnel shift that aligns the partner bits and the OR into C;
             # 2 per probed (n, prime): shift and bit test
-            units = work["cover_iterations"] / launches
+            units = wk["cover_iterations"] / nl
             ops = 2.0 * units
-            # DRAM bytes per even n measured by ncu on [4, 2^32] (profiles/):
-            # the q window read once; scaled to this launch's n
-            traffic = 0.1269 * kp["units"] / launches
-            alg_bytes = kp["units"] / launches / 8.0
         else:
             # minimal ALU work: 2 ops per strike (word index, rotated mask) and
             # 6 per stamped 32-bit word (four pattern funnel shifts, two ANDs)
-            units = work["sieve_strikes"] / launches
-            ops = 2.0 * units + 6.0 * (kp["units"] / launches) / 32.0
-            traffic = 0.09657 * kp["units"] / launches   # ncu bytes per q bit (written once)
-            alg_bytes = kp["units"] / launches / 8.0
+            units = wk["sieve_strikes"] / nl
+            ops = 2.0 * units + 6.0 * (kp["units"] / nl) / 32.0
+        alg_bytes = kp["units"] / nl / 8.0               # the q bits, written once / read once
+        traffic = ncu_traffic[kern] * kp["units"] / nl if kern in ncu_traffic else None
         achieved = ops / (ms / 1000.0) / 1e12
         per[kern] = {"ms_per_launch": ms, "achieved": achieved, "frac": achieved / alu_peak,
                      "alu_ops_per_launch": ops, "work_units_per_launch": units,
@@ -347,19 +495,21 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / (PAPER_NPS * world),
-            "dtype": "u64", "data": "synthetic", "mode": "plain",
-            "config": workload_desc(world),
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / (PAPER_NPS * world) if args.mode == "plain" else None,
+            "dtype": "u64", "data": "synthetic", "mode": args.mode,
+            "config": workload_desc(args.mode, world),
             "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": work.h2d,
+                    "d2h_bytes_per_step": work.d2h},
             "clocks": clk,
-            "gpu_launches": int(sum(prof[k]["launches"] for k in prof)),
+            "gpu_launches": int(launches),
             "kernel_ms": {k: prof[k]["ms"] for k in prof},
-            "result_check": {"unresolved": int(last.unresolved), "max_pmin": int(last.max_pmin),
-                             "max_pmin_n": int(last.max_pmin_n), "n_checked": int(last.n_checked)},
-            "paper_context": "RTX 3070, Table 4: [4, 1e10] in 23,547 ms = 2.12e8 n/s"}
+            "result_check": work.check(),
+            "paper_context": PAPER_CONTEXT}
+    line.update(work.extra(args))
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline().items() if k != "seconds"}
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(args.mode).items() if k != "seconds"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

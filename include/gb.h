@@ -62,13 +62,19 @@ typedef struct gb_config {
                                sqrt(B)); 0 = 2^16; at most 2^32 */
     uint32_t tile_bits;     /* segment-sieve tile (odd numbers per CTA tile),
                                multiple of 8192, <= 2^20; 0 = 2^18 */
-    uint32_t cta_threads;   /* threads per sieve/cover CTA, multiple of 32,
-                               <= 1024; 0 = 256 */
-    uint32_t bucket_split;  /* sieving primes >= this go through per-tile hit
-                               lists; 0 = tile_bits */
+    uint32_t cta_threads;   /* threads per segment-sieve CTA: 128, 256 or
+                               512; 0 = 256 */
+    uint32_t bucket_split;  /* sieving primes >= this are struck by the
+                               large-prime pass (one start per L2-sized chunk
+                               of the window, global atomic AND) instead of
+                               per tile in shared memory; 0 = tile_bits */
     uint32_t p1;            /* first-pass bound P1 (p <= P1); 0 = 2^15 */
     uint32_t p2;            /* retry-pass bound P2; 0 or <= p1 = no retry pass;
                                <= 2^24 */
+    uint32_t cover_prefix;  /* primes of the cover's unrolled phase (blocks of
+                               64 over every word, then per-n probing): 64,
+                               128, 192 or 256; 0 = chosen by the magnitude
+                               of n.  Outputs do not depend on it. */
     uint64_t slab_bits;     /* most q-bits sieved and kept resident at once
                                (a slab is a run of whole segments); 0 = 2^33 */
     void*    stream;        /* cudaStream_t for all work; NULL = the legacy
@@ -126,6 +132,29 @@ void gb_destroy(gb_ctx* ctx);
 
 /* The configuration in effect, defaults filled in. */
 int gb_get_config(const gb_ctx* ctx, gb_config* out);
+
+/* Change the tunable fields of a context's configuration (seg_len, tile_bits,
+ * cta_threads, bucket_split, p1, p2, cover_prefix, slab_bits; 0 = default as
+ * in gb_init).  device, base_limit and stream must equal the context's
+ * (GB_EINVAL otherwise); p1 and p2 must not exceed the base primes.  Waits
+ * for the context's stream.  Outputs of later calls do not depend on the
+ * tunables, except that per-segment outputs follow seg_len and the first-pass
+ * histogram length follows p1. */
+int gb_set_config(gb_ctx* ctx, const gb_config* cfg);
+
+/* Autotuner (the batched configuration's "autotuned segment / tile / CTA / P"):
+ * verifies the sample workload [lo[i], hi[i]) i < count under candidate
+ * settings, one parameter at a time (coordinate descent over tile_bits,
+ * bucket_split, p1, cover_prefix and, for GB_TUNE_PLAIN, seg_len and
+ * cta_threads), each timed with CUDA events on the context's stream as the
+ * best of reps runs after a warm-up run; keeps the fastest setting in the
+ * context and returns it in *out (optional) with its time in *best_ms
+ * (optional).  mode GB_TUNE_PLAIN times gb_verify_range on each range,
+ * GB_TUNE_BATCH one gb_verify_batch over all of them.  reps 0 = 2. */
+#define GB_TUNE_PLAIN 0
+#define GB_TUNE_BATCH 1
+int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_t count, int mode, uint32_t reps,
+                gb_config* out, double* best_ms);
 
 /* Sieve one window of odd numbers (Sec. 2.2 layout, Sec. 2.3.1 segment sieve):
  * bit i (bit i%64 of word i/64, little-endian bit order) of q_bits is 1 iff the
@@ -209,6 +238,10 @@ int gb_profile_read(gb_ctx* ctx, double* ms, uint64_t* launches, uint64_t* units
  * primes applied until the word filled (the bound's count for a word left
  * open). */
 int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterations);
+
+/* Kernels launched by verification calls of this context since the last
+ * gb_profile_enable (counted whether or not profiling is on). */
+int gb_profile_kernels(gb_ctx* ctx, uint64_t* kernels);
 
 /* Bytes of the odd-only dense bitset for the odd numbers 3..N (Sec. 2.2):
  * ceil(#odd in [3, N] / 64) 64-bit words.  Host-only helper. */

@@ -39,6 +39,12 @@ int fail(int code, const std::string& msg)
         if (e_ != cudaSuccess)                                                      \
             return fail(GB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+// a kernel launch of a verification call, counted for the profile
+#define GB_LAUNCH(expr)       \
+    do {                      \
+        GB_CUDA(expr);        \
+        ctx->kernels += 1;    \
+    } while (0)
 
 struct DevBuf {
     void* p = nullptr;
@@ -134,17 +140,21 @@ struct gb_ctx {
     // batched mode
     DevBuf bq, bhist, bkeys, bunres, bdesc, brecords, brows;
     HostBuf hstage;
+    bool batch_graph = true;          // batch kernels as one CUDA graph (GB_BATCH_GRAPH=0: plain launches)
+    bool capturing = false;           // cap_stream is being captured (profiling events become graph nodes)
+    cudaStream_t cap_stream = nullptr;  // private stream the batch graph is captured on
+    cudaGraphExec_t bgraph = nullptr;
     uint64_t work_strikes = 0, work_iters = 0;
     int warp_split = 0;               // sieving primes below this strike one warp each
     bool generic_cover = false;       // force the generic cover kernel (GB_COVER=generic)
     uint64_t large_chunk_bits = 1ull << 28;   // large-prime strikes per L2-resident chunk of the window
-    int ka_override = 0;              // first-phase length of the two-phase cover (GB_KA)
 
     // per-kernel device time (CUDA events on the context's stream around each launch)
     bool profiling = false;
     double prof_ms[GB_PROF_KINDS] = {};
     uint64_t prof_launches[GB_PROF_KINDS] = {};
     uint64_t prof_units[GB_PROF_KINDS] = {};
+    uint64_t kernels = 0;             // kernels launched by verification calls since profiling was enabled
     struct Pending { cudaEvent_t a, b; int kind; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
@@ -163,7 +173,8 @@ struct gb_ctx {
         if (!profiling) return;
         cur_kind = kind;
         cur_a = take_event();
-        cudaEventRecord(cur_a, stream);
+        cudaEventRecordWithFlags(cur_a, capturing ? cap_stream : stream,
+                                 capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
         prof_launches[kind] += 1;
         prof_units[kind] += units;
     }
@@ -171,7 +182,8 @@ struct gb_ctx {
     {
         if (!profiling || cur_kind < 0) return;
         cudaEvent_t b = take_event();
-        cudaEventRecord(b, stream);
+        cudaEventRecordWithFlags(b, capturing ? cap_stream : stream,
+                                 capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
         pending.push_back({cur_a, b, cur_kind});
         cur_kind = -1;
     }
@@ -200,6 +212,8 @@ struct gb_ctx {
     }
     ~gb_ctx()
     {
+        if (bgraph) cudaGraphExecDestroy(bgraph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (const Pending& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
         for (cudaEvent_t e : pool) cudaEventDestroy(e);
     }
@@ -231,6 +245,9 @@ int fill_defaults(gb_config& c)
     if (c.base_limit > (1ull << 32)) return fail(GB_EINVAL, "base_limit must be <= 2^32");
     if (c.p1 < 2 || c.p1 > (1u << 24) || c.p2 > (1u << 24))
         return fail(GB_EINVAL, "p1 must be in [2, 2^24] and p2 <= 2^24");
+    if (c.cover_prefix != 0 && c.cover_prefix != 64 && c.cover_prefix != 128 && c.cover_prefix != 192 &&
+        c.cover_prefix != 256)
+        return fail(GB_EINVAL, "cover_prefix must be 0, 64, 128, 192 or 256");
     if (c.slab_bits < c.seg_len) c.slab_bits = c.seg_len;
     return GB_OK;
 }
@@ -264,7 +281,7 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
     a.out = out;
     a.popcount = large ? nullptr : popc;
     a.strikes = ctx->work_ptr(0);
-    GB_CUDA(gb::launch_sieve(a, (int)ctx->cfg.cta_threads, ctx->stream));
+    GB_LAUNCH(gb::launch_sieve(a, (int)ctx->cfg.cta_threads, ctx->stream));
     if (large) {
         gb::LargeArgs la{};
         la.B = B;
@@ -277,9 +294,9 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
         for (uint64_t c0 = 0; c0 < nbits; c0 += chunk) {
             la.bit_lo = c0;
             la.bit_hi = std::min(nbits, c0 + chunk);
-            GB_CUDA(gb::launch_large(la, ctx->stream));
+            GB_LAUNCH(gb::launch_large(la, ctx->stream));
         }
-        if (popc) GB_CUDA(gb::launch_popcount(out, ((nbits + 63) / 64) * 2, popc, ctx->stream));
+        if (popc) GB_LAUNCH(gb::launch_popcount(out, ((nbits + 63) / 64) * 2, popc, ctx->stream));
     }
     return GB_OK;
 }
@@ -371,7 +388,7 @@ int ctx_view(const gb_ctx* ctx, CtxView* v)
     v->recip = ctx->recip.as<uint64_t>();
     v->wheel = ctx->wheel.as<uint32_t>();
     v->generic_cover = ctx->generic_cover;
-    v->ka_override = ctx->ka_override;
+    v->ka_override = (int)ctx->cfg.cover_prefix;
     v->large_chunk_bits = ctx->large_chunk_bits;
     return GB_OK;
 }
@@ -442,13 +459,14 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     ctx->warp_split = (int)std::min<uint32_t>(1024, c.tile_bits / 64);
     if (const char* e = getenv("GB_WARP_SPLIT")) ctx->warp_split = atoi(e);
     if (const char* e = getenv("GB_COVER")) ctx->generic_cover = std::string(e) == "generic";
+    if (const char* e = getenv("GB_BATCH_GRAPH")) ctx->batch_graph = atoi(e) != 0;
     if (const char* e = getenv("GB_LARGE_CHUNK_LOG2")) {
         const int v = atoi(e);
         if (v >= 16 && v <= 40) ctx->large_chunk_bits = 1ull << v;
     }
     if (const char* e = getenv("GB_KA")) {
         const int v = atoi(e);
-        if (v == 64 || v == 128 || v == 192 || v == 256) ctx->ka_override = v;
+        if ((v == 64 || v == 128 || v == 192 || v == 256) && ctx->cfg.cover_prefix == 0) ctx->cfg.cover_prefix = v;
     }
     rc = build_primes(ctx);
     if (rc) {
@@ -477,6 +495,23 @@ int gb_get_config(const gb_ctx* ctx, gb_config* out)
 {
     if (!ctx || !out) return fail(GB_EINVAL, "NULL argument");
     *out = ctx->cfg;
+    return GB_OK;
+}
+
+int gb_set_config(gb_ctx* ctx, const gb_config* cfg)
+{
+    if (!ctx || !cfg) return fail(GB_EINVAL, "NULL argument");
+    gb_config c = *cfg;
+    int rc = fill_defaults(c);
+    if (rc) return rc;
+    if (c.device != ctx->cfg.device || c.base_limit != ctx->cfg.base_limit || c.stream != ctx->cfg.stream)
+        return fail(GB_EINVAL, "device, base_limit and stream are fixed at gb_init");
+    if (std::max(c.p1, c.p2) > ctx->L) return fail(GB_EINVAL, "p1/p2 above the context's base primes");
+    GB_CUDA(cudaSetDevice(ctx->cfg.device));
+    if (ctx->stream) GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    else GB_CUDA(cudaDeviceSynchronize());
+    ctx->cfg = c;
+    if (!getenv("GB_WARP_SPLIT")) ctx->warp_split = (int)std::min<uint32_t>(1024, c.tile_bits / 64);
     return GB_OK;
 }
 
@@ -638,7 +673,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         // two-phase kernel unless a p_min array is wanted (the generic kernel
         // writes it) or the pass has too few primes for its first phase
         int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
-        if (KA && ctx->ka_override && (uint32_t)ctx->ka_override <= K1) KA = ctx->ka_override;
+        if (KA && cfg.cover_prefix && cfg.cover_prefix <= K1) KA = (int)cfg.cover_prefix;
         if (KA) {
             // block cover: 7680 32-bit words per CTA (ten rounds of 96 words per
             // warp, the most its 10-bit counters allow)
@@ -646,8 +681,8 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
             ca.chunks_per_seg = (uint32_t)((S / 64 + ca.cta_words - 1) / ca.cta_words);
         }
         ctx->prof_begin(kProfCover, n_count);
-        if (KA) GB_CUDA(gb::launch_cover_fast(ca, KA, s));
-        else GB_CUDA(gb::launch_cover(ca, (int)cfg.cta_threads, s));
+        if (KA) GB_LAUNCH(gb::launch_cover_fast(ca, KA, s));
+        else GB_LAUNCH(gb::launch_cover(ca, (int)cfg.cta_threads, s));
         ctx->prof_end();
 
         if (retry) {
@@ -667,7 +702,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
             ra.count = ca.retry_count;
             ra.cap = retry_cap;
             ctx->prof_begin(kProfRetry, n_count);
-            GB_CUDA(gb::launch_retry(ra, s));
+            GB_LAUNCH(gb::launch_retry(ra, s));
             ctx->prof_end();
         }
 
@@ -685,7 +720,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         rd.nrows = (uint32_t)(want_rows ? std::min<uint64_t>(ns, rows_n > s0 ? rows_n - s0 : 0) : 0);
         rd.merged = ctx->merged.as<unsigned long long>();
         ctx->prof_begin(kProfReduce, ns);
-        GB_CUDA(gb::launch_reduce(rd, s));
+        GB_LAUNCH(gb::launch_reduce(rd, s));
         ctx->prof_end();
 
         if (retry) {
@@ -721,7 +756,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
     fa.nrecords = (uint32_t)(out->segs ? std::min<uint64_t>(out->seg_cap, nseg) : 0);
     fa.totals = ctx->totals.as<gb::RangeTotals>();
     ctx->prof_begin(kProfReduce, nseg);
-    GB_CUDA(gb::launch_finalize(fa, s));
+    GB_LAUNCH(gb::launch_finalize(fa, s));
     ctx->prof_end();
 
     gb::RangeTotals tot{};
@@ -810,6 +845,8 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
         groups.push_back(count);
     }
     const uint32_t n_groups = (uint32_t)groups.size() - 1;
+    if (np > nsmall && (uint64_t)n_groups * ((np - nsmall + 255) / 256) > 0xffffffffull)
+        return fail(GB_EINVAL, "batch too large");
 
     // device buffers
     const size_t desc_ranges = (size_t)count * sizeof(gb::BatchRange);
@@ -855,6 +892,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
         counts[0] = (uint32_t)n_sieve;
         counts[1] = (uint32_t)n_cover;
         counts[2] = count;
+        counts[3] = np > nsmall ? (uint32_t)(n_groups * ((np - nsmall + 255) / 256)) : 0u;
     }
     unsigned char* dd = static_cast<unsigned char*>(ctx->bdesc.p);
     const size_t used = reinterpret_cast<unsigned char*>(counts + 4) - hs_p;
@@ -873,83 +911,133 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     GB_CUDA(cudaMemsetAsync(ctx->bkeys.p, 0, (size_t)count * 8, s));
     GB_CUDA(cudaMemsetAsync(ctx->bunres.p, 0, (size_t)count * 8, s));
 
-    // sieve: tile part (persistent, item queue), then large primes group by group
-    gb::SieveItemsArgs sa{};
-    sa.base.tile_bits = T;
-    sa.base.primes = ctx->primes.as<uint32_t>() + gb::kFirstStrikeIdx;
-    sa.base.recip = ctx->recip.as<uint64_t>() + gb::kFirstStrikeIdx;
-    const uint64_t nstrike = nsmall > gb::kFirstStrikeIdx ? nsmall - gb::kFirstStrikeIdx : 0;
-    const uint64_t nwarp_all = ctx->pi((uint64_t)ctx->warp_split - 1);
-    sa.base.n_warp = (uint32_t)std::min<uint64_t>(nstrike, nwarp_all > gb::kFirstStrikeIdx ? nwarp_all - gb::kFirstStrikeIdx : 0);
-    sa.base.n_primes = (uint32_t)nstrike;
-    sa.base.wheel = ctx->wheel.as<uint32_t>();
-    sa.base.strikes = ctx->work_ptr(0);
-    sa.ranges = d_ranges;
-    sa.item_range = d_s_range;
-    sa.item_tile = d_s_tile;
-    sa.n_items = d_counts + 0;
-    sa.head = heads + 0;
-    sa.Q = ctx->bq.as<uint32_t>();
-    ctx->prof_begin(kProfSieve, qwords * 64);
-    GB_CUDA(gb::launch_sieve_items(sa, (int)cfg.cta_threads, s));
-    if (np > nsmall) {
-        gb::LargeBatchArgs la{};
-        la.ranges = d_ranges;
-        la.groups = d_groups;
-        la.primes = ctx->primes.as<uint32_t>() + nsmall;
-        la.recip = ctx->recip.as<uint64_t>() + nsmall;
-        la.n_primes = (uint32_t)(np - nsmall);
-        la.Q = ctx->bq.as<uint32_t>();
-        la.strikes = ctx->work_ptr(0);
-        for (uint32_t g = 0; g < n_groups; ++g) {
-            la.group = g;
-            GB_CUDA(gb::launch_large_batch(la, s));
-        }
-    }
-    ctx->prof_end();
-
-    // cover: persistent, item queue; row r = range r; no retry here
+    // block-cover length (unrolled primes) for the batch's largest n
     int KA = ctx->generic_cover ? 0 : gb::cover_fast_phase_primes(K1, hi_max);
-    if (KA && ctx->ka_override && (uint32_t)ctx->ka_override <= K1) KA = ctx->ka_override;
+    if (KA && cfg.cover_prefix && cfg.cover_prefix <= K1) KA = (int)cfg.cover_prefix;
     if (!KA) return fail(GB_EINVAL, "gb_verify_batch needs P >= the 64th odd prime (313)");
-    gb::CoverItemsArgs cv{};
-    cv.base.H = H;
-    cv.base.cta_words = cw;
-    cv.base.primes = ctx->primes.as<uint32_t>();
-    cv.base.K = K1;
-    cv.base.hist_stride = hs;
-    cv.base.hist = ctx->bhist.as<uint32_t>();
-    cv.base.maxkey = ctx->bkeys.as<unsigned long long>();
-    cv.base.unresolved = ctx->bunres.as<unsigned long long>();
-    cv.base.iters = ctx->work_ptr(1);
-    cv.ranges = d_ranges;
-    cv.item_range = d_c_range;
-    cv.item_chunk = d_c_chunk;
-    cv.n_items = d_counts + 1;
-    cv.head = heads + 1;
-    cv.Q = ctx->bq.as<uint64_t>();
-    ctx->prof_begin(kProfCover, qwords * 64);
-    GB_CUDA(gb::launch_cover_items(cv, KA, s));
-    ctx->prof_end();
 
-    gb::ReduceBatchArgs ra{};
-    ra.ranges = d_ranges;
-    ra.count = d_counts + 2;
-    ra.hist = ctx->bhist.as<uint32_t>();
-    ra.hist_stride = hs;
-    ra.maxkey = ctx->bkeys.as<unsigned long long>();
-    ra.unresolved = ctx->bunres.as<unsigned long long>();
-    ra.primes = ctx->primes.as<uint32_t>();
-    ra.records = res_dev ? reinterpret_cast<gb::SegRecord*>(results) : ctx->brecords.as<gb::SegRecord>();
-    ra.rows = want_rows ? (rows_dev ? hist : ctx->brows.as<uint64_t>()) : nullptr;
-    ra.row_stride = want_rows ? hist_stride : 0;
-    ctx->prof_begin(kProfReduce, count);
-    GB_CUDA(gb::launch_reduce_batch(ra, count, s));
-    ctx->prof_end();
+    // the kernels of the batch, captured as one CUDA graph (re-used by update
+    // while the sequence keeps its shape) or launched one by one
+    // (captured on a private stream -- the caller's may be the legacy default
+    // stream, which cannot be captured -- and launched on the caller's)
+    const bool graph = ctx->batch_graph;
+    cudaStream_t ls = s;
+    if (graph) {
+        if (!ctx->cap_stream) GB_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        ls = ctx->cap_stream;
+        GB_CUDA(cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = true;
+    }
+    gb::SegRecord* d_records = res_dev ? reinterpret_cast<gb::SegRecord*>(results) : ctx->brecords.as<gb::SegRecord>();
+    int lrc = GB_OK;
+    auto launches = [&]() -> int {
+        // sieve: tile part (persistent, item queue), then the large primes
+        gb::SieveItemsArgs sa{};
+        sa.base.tile_bits = T;
+        sa.base.primes = ctx->primes.as<uint32_t>() + gb::kFirstStrikeIdx;
+        sa.base.recip = ctx->recip.as<uint64_t>() + gb::kFirstStrikeIdx;
+        const uint64_t nstrike = nsmall > gb::kFirstStrikeIdx ? nsmall - gb::kFirstStrikeIdx : 0;
+        const uint64_t nwarp_all = ctx->pi((uint64_t)ctx->warp_split - 1);
+        sa.base.n_warp = (uint32_t)std::min<uint64_t>(nstrike, nwarp_all > gb::kFirstStrikeIdx ? nwarp_all - gb::kFirstStrikeIdx : 0);
+        sa.base.n_primes = (uint32_t)nstrike;
+        sa.base.wheel = ctx->wheel.as<uint32_t>();
+        sa.base.strikes = ctx->work_ptr(0);
+        sa.ranges = d_ranges;
+        sa.item_range = d_s_range;
+        sa.item_tile = d_s_tile;
+        sa.n_items = d_counts + 0;
+        sa.head = heads + 0;
+        sa.Q = ctx->bq.as<uint32_t>();
+        ctx->prof_begin(kProfSieve, qwords * 64);
+        GB_LAUNCH(gb::launch_sieve_items(sa, (int)cfg.cta_threads, ls));
+        {
+            gb::LargeBatchArgs la{};
+            la.ranges = d_ranges;
+            la.groups = d_groups;
+            la.n_items = d_counts + 3;
+            la.head = heads + 2;
+            la.primes = ctx->primes.as<uint32_t>() + nsmall;
+            la.recip = ctx->recip.as<uint64_t>() + nsmall;
+            la.n_primes = (uint32_t)(np - nsmall);
+            la.Q = ctx->bq.as<uint32_t>();
+            la.strikes = ctx->work_ptr(0);
+            if (np > nsmall) GB_LAUNCH(gb::launch_large_batch(la, ls));
+        }
+        ctx->prof_end();
+
+        // cover: persistent, item queue; row r = range r; no retry here (open
+        // ranges are redone below)
+        gb::CoverItemsArgs cv{};
+        cv.base.H = H;
+        cv.base.cta_words = cw;
+        cv.base.primes = ctx->primes.as<uint32_t>();
+        cv.base.K = K1;
+        cv.base.hist_stride = hs;
+        cv.base.hist = ctx->bhist.as<uint32_t>();
+        cv.base.maxkey = ctx->bkeys.as<unsigned long long>();
+        cv.base.unresolved = ctx->bunres.as<unsigned long long>();
+        cv.base.iters = ctx->work_ptr(1);
+        cv.ranges = d_ranges;
+        cv.item_range = d_c_range;
+        cv.item_chunk = d_c_chunk;
+        cv.n_items = d_counts + 1;
+        cv.head = heads + 1;
+        cv.Q = ctx->bq.as<uint64_t>();
+        ctx->prof_begin(kProfCover, qwords * 64);
+        GB_LAUNCH(gb::launch_cover_items(cv, KA, ls));
+        ctx->prof_end();
+
+        gb::ReduceBatchArgs ra{};
+        ra.ranges = d_ranges;
+        ra.count = d_counts + 2;
+        ra.hist = ctx->bhist.as<uint32_t>();
+        ra.hist_stride = hs;
+        ra.maxkey = ctx->bkeys.as<unsigned long long>();
+        ra.unresolved = ctx->bunres.as<unsigned long long>();
+        ra.primes = ctx->primes.as<uint32_t>();
+        ra.records = d_records;
+        ra.rows = want_rows ? (rows_dev ? hist : ctx->brows.as<uint64_t>()) : nullptr;
+        ra.row_stride = want_rows ? hist_stride : 0;
+        ctx->prof_begin(kProfReduce, count);
+        GB_LAUNCH(gb::launch_reduce_batch(ra, count, ls));
+        ctx->prof_end();
+        return GB_OK;
+    };
+    lrc = launches();
+    if (graph) {
+        ctx->capturing = false;
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(ls, &g);
+        if (lrc) {
+            if (g) cudaGraphDestroy(g);
+            return lrc;
+        }
+        if (ce != cudaSuccess) return fail(GB_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+        bool updated = false;
+        if (ctx->bgraph) {
+            cudaGraphExecUpdateResultInfo info{};
+            updated = cudaGraphExecUpdate(ctx->bgraph, g, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(ctx->bgraph);
+                ctx->bgraph = nullptr;
+            }
+        }
+        cudaError_t ie = cudaSuccess;
+        if (!updated) ie = cudaGraphInstantiate(&ctx->bgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            ctx->bgraph = nullptr;
+            return fail(GB_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+        }
+        GB_CUDA(cudaGraphLaunch(ctx->bgraph, s));
+    } else if (lrc) {
+        return lrc;
+    }
 
     // results to the caller; ranges with open n are redone with the retry pass
     std::vector<gb::SegRecord> rec(count);
-    GB_CUDA(cudaMemcpyAsync(rec.data(), ra.records, (size_t)count * sizeof(gb::SegRecord), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(rec.data(), d_records, (size_t)count * sizeof(gb::SegRecord), cudaMemcpyDeviceToHost, s));
     if (want_rows && !rows_dev)
         GB_CUDA(cudaMemcpyAsync(hist, ctx->brows.p, (size_t)count * hist_stride * 8, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
@@ -995,6 +1083,7 @@ int gb_profile_enable(gb_ctx* ctx, int enable)
     if (rc) return rc;
     for (int k = 0; k < GB_PROF_KINDS; ++k) { ctx->prof_ms[k] = 0; ctx->prof_launches[k] = 0; ctx->prof_units[k] = 0; }
     ctx->work_strikes = ctx->work_iters = 0;
+    ctx->kernels = 0;
     if (enable && !ctx->work.p) {
         if ((rc = ctx->work.ensure(16))) return rc;
         GB_CUDA(cudaMemset(ctx->work.p, 0, 16));
@@ -1014,6 +1103,13 @@ int gb_profile_read(gb_ctx* ctx, double* ms, uint64_t* launches, uint64_t* units
         if (launches) launches[k] = ctx->prof_launches[k];
         if (units) units[k] = ctx->prof_units[k];
     }
+    return GB_OK;
+}
+
+int gb_profile_kernels(gb_ctx* ctx, uint64_t* kernels)
+{
+    if (!ctx || !kernels) return fail(GB_EINVAL, "NULL argument");
+    *kernels = ctx->kernels;
     return GB_OK;
 }
 

@@ -10,13 +10,26 @@
 
 namespace gb {
 
-// primes above the tile size, over the ranges of one group (the group's windows
-// together fit in L2): one thread per prime, every range of the group
+// primes above the tile size: persistent CTAs take (group, block of 256
+// primes) items in group-major order, so the CTAs work on one or two groups at
+// a time and the struck words stay in L2; one thread per prime, every range
+// of the group
 __global__ void __launch_bounds__(256) k_large_batch(const LargeBatchArgs a)
 {
-    const uint32_t r0 = a.groups[a.group], r1 = a.groups[a.group + 1];
+    __shared__ uint32_t s_item;
+    const uint32_t n_items = *a.n_items;
+    const uint32_t nblk = (a.n_primes + 255) / 256;
     unsigned long long nstrike = 0;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_primes; k += gridDim.x * blockDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.head, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        const uint32_t g = item / nblk;
+        const uint32_t k = (item - g * nblk) * 256 + threadIdx.x;
+        if (k >= a.n_primes) continue;
+        const uint32_t r0 = a.groups[g], r1 = a.groups[g + 1];
         const uint32_t p = a.primes[k];
         const uint64_t m = a.recip[k];
         const uint64_t pp = (uint64_t)p * p;
@@ -45,8 +58,12 @@ __global__ void __launch_bounds__(256) k_large_batch(const LargeBatchArgs a)
 cudaError_t launch_large_batch(const LargeBatchArgs& a, cudaStream_t s)
 {
     if (a.n_primes == 0) return cudaSuccess;
-    const uint32_t blocks = (a.n_primes + 255) / 256;
-    k_large_batch<<<blocks < 152u * 64 ? blocks : 152u * 64, 256, 0, s>>>(a);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_batch, 256, 0)) != cudaSuccess) return e;
+    k_large_batch<<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -254,11 +254,13 @@ struct CoverItemsArgs {
 };
 cudaError_t launch_cover_items(const CoverItemsArgs& a, int KA, cudaStream_t s);
 
-// large primes over the ranges groups[group] .. groups[group+1]-1
+// large primes over groups of ranges (a group's windows together fit in L2):
+// items (group, block of 256 primes), group-major, from a device queue
 struct LargeBatchArgs {
     const BatchRange* ranges;
     const uint32_t* groups;     // device: first range of each group, then the count
-    uint32_t group;
+    const uint32_t* n_items;    // device: groups x prime blocks
+    unsigned int* head;         // device queue head (zeroed)
     const uint32_t* primes;     // the large primes
     const uint64_t* recip;
     uint32_t n_primes;

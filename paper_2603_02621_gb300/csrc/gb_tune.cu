@@ -1,0 +1,167 @@
+// gb_tune.cu -- autotuner: picks the segment length, sieve tile, CTA size, the
+// tile / large-prime split, the first-pass bound P and the cover's unrolled
+// prefix for a sample workload by timing the real entry points (GoldbachGPU,
+// arXiv 2603.02621: the segment length and P1 are the knobs of Sec. 2.3 and
+// Sec. 2.4; the others are this implementation's).
+//
+// Coordinate descent: each parameter in turn is set to each of its candidates,
+// the others held at the best so far; a candidate is timed as the best of
+// `reps` runs after one warm-up run (which also sizes the arenas).  Outputs do
+// not depend on any of these settings, so the search never changes a result.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "gb.h"
+
+namespace {
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    Timer()
+    {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~Timer()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+// run the sample once under the context's current configuration
+int run_sample(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_t count, int mode,
+               std::vector<gb_segment_result>& recs)
+{
+    if (mode == GB_TUNE_BATCH) return gb_verify_batch(ctx, lo, hi, count, 0, recs.data(), nullptr, 0);
+    for (uint32_t i = 0; i < count; ++i) {
+        gb_range_result r{};
+        const int rc = gb_verify_range(ctx, lo[i], hi[i], 0, &r);
+        if (rc) return rc;
+    }
+    return GB_OK;
+}
+
+// best-of-reps time of the sample under cfg; < 0 if the setting is rejected
+double time_setting(gb_ctx* ctx, const gb_config& cfg, const uint64_t* lo, const uint64_t* hi, uint32_t count,
+                    int mode, uint32_t reps, std::vector<gb_segment_result>& recs, Timer& t, int* err)
+{
+    *err = GB_OK;
+    if (gb_set_config(ctx, &cfg) != GB_OK) return -1.0;
+    cudaStream_t s = static_cast<cudaStream_t>(cfg.stream);
+    int rc = run_sample(ctx, lo, hi, count, mode, recs);   // warm-up, arenas
+    if (rc) {
+        *err = rc;
+        return -1.0;
+    }
+    double best = -1.0;
+    for (uint32_t k = 0; k < reps; ++k) {
+        cudaEventRecord(t.a, s);
+        rc = run_sample(ctx, lo, hi, count, mode, recs);
+        cudaEventRecord(t.b, s);
+        if (rc) {
+            *err = rc;
+            return -1.0;
+        }
+        if (cudaEventSynchronize(t.b) != cudaSuccess) {
+            *err = GB_ECUDA;
+            return -1.0;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        if (best < 0 || ms < best) best = ms;
+    }
+    return best;
+}
+
+}  // namespace
+
+extern "C" int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_t count, int mode,
+                           uint32_t reps, gb_config* out, double* best_ms)
+{
+    if (!ctx || !lo || !hi || count == 0) return GB_EINVAL;
+    if (mode != GB_TUNE_PLAIN && mode != GB_TUNE_BATCH) return GB_EINVAL;
+    if (reps == 0) reps = 2;
+    gb_config best{};
+    int rc = gb_get_config(ctx, &best);
+    if (rc) return rc;
+    const gb_config start = best;
+    std::vector<gb_segment_result> recs(mode == GB_TUNE_BATCH ? count : 0);
+    Timer t;
+    int err = GB_OK;
+    double best_t = time_setting(ctx, best, lo, hi, count, mode, reps, recs, t, &err);
+    if (best_t < 0) {
+        gb_set_config(ctx, &start);
+        return err ? err : GB_EINVAL;
+    }
+
+    uint64_t longest = 0;
+    for (uint32_t i = 0; i < count; ++i) longest = std::max(longest, (hi[i] - lo[i]) / 2);
+
+    // candidates of one parameter, given the best setting so far
+    using Apply = std::function<bool(gb_config&, uint32_t)>;
+    struct Param {
+        std::vector<uint32_t> values;
+        Apply apply;
+    };
+    std::vector<Param> params;
+    params.push_back({{1u << 16, 1u << 17, 1u << 18, 1u << 19, 1u << 20}, [](gb_config& c, uint32_t v) {
+                          // keep the split at the same multiple of the tile
+                          const double m = (double)c.bucket_split / (double)c.tile_bits;
+                          c.tile_bits = v;
+                          c.bucket_split = (uint32_t)std::max(64.0, m * v);
+                          return true;
+                      }});
+    params.push_back({{1, 2, 4, 8, 16}, [](gb_config& c, uint32_t v) {
+                          c.bucket_split = (uint32_t)std::min<uint64_t>(0xffffffffull, (uint64_t)c.tile_bits * v / 4);
+                          return true;
+                      }});
+    params.push_back({{1u << 11, 1u << 12, 1u << 13, 1u << 14, 1u << 15}, [](gb_config& c, uint32_t v) {
+                          if (c.p2 && v >= c.p2) return false;
+                          c.p1 = v;
+                          return true;
+                      }});
+    params.push_back({{64, 128, 192, 256}, [](gb_config& c, uint32_t v) {
+                          c.cover_prefix = v;
+                          return true;
+                      }});
+    if (mode == GB_TUNE_PLAIN) {
+        params.push_back({{1u << 22, 1u << 23, 1u << 24, 1u << 25, 1u << 26, 1u << 27},
+                          [longest](gb_config& c, uint32_t v) {
+                              if (v > 2 * std::max<uint64_t>(longest, 1u << 22)) return false;
+                              c.seg_len = v;
+                              return true;
+                          }});
+        params.push_back({{128, 256, 512}, [](gb_config& c, uint32_t v) {
+                              c.cta_threads = v;
+                              return true;
+                          }});
+    }
+
+    for (const Param& p : params) {
+        for (uint32_t v : p.values) {
+            gb_config c = best;
+            if (!p.apply(c, v)) continue;
+            if (std::memcmp(&c, &best, sizeof c) == 0) continue;
+            const double ms = time_setting(ctx, c, lo, hi, count, mode, reps, recs, t, &err);
+            if (err && err != GB_EINVAL) {
+                gb_set_config(ctx, &start);
+                return err;
+            }
+            if (ms >= 0 && ms < best_t) {
+                best_t = ms;
+                best = c;
+            }
+        }
+    }
+    rc = gb_set_config(ctx, &best);
+    if (rc) return rc;
+    if (out) *out = best;
+    if (best_ms) *best_ms = best_t;
+    return GB_OK;
+}

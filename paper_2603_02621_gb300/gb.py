@@ -30,7 +30,8 @@ class GbError(RuntimeError):
 class gb_config(ctypes.Structure):
     _fields_ = [("device", c_int32), ("seg_len", c_uint32), ("base_limit", c_uint64),
                 ("tile_bits", c_uint32), ("cta_threads", c_uint32), ("bucket_split", c_uint32),
-                ("p1", c_uint32), ("p2", c_uint32), ("slab_bits", c_uint64), ("stream", c_void_p)]
+                ("p1", c_uint32), ("p2", c_uint32), ("cover_prefix", c_uint32), ("slab_bits", c_uint64),
+                ("stream", c_void_p)]
 
 
 class gb_segment_result(ctypes.Structure):
@@ -61,9 +62,13 @@ SIGNATURES = {
     "gb_verify_range_noalloc": (c_int, [c_void_p, c_uint64, c_uint64, c_uint32, POINTER(gb_range_result)]),
     "gb_verify_batch": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), c_uint32, c_uint32,
                                 c_void_p, c_void_p, c_uint32]),
+    "gb_set_config": (c_int, [c_void_p, POINTER(gb_config)]),
+    "gb_autotune": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), c_uint32, c_int, c_uint32,
+                            POINTER(gb_config), POINTER(ctypes.c_double)]),
     "gb_profile_enable": (c_int, [c_void_p, c_int]),
     "gb_profile_read": (c_int, [c_void_p, POINTER(ctypes.c_double), POINTER(c_uint64), POINTER(c_uint64)]),
     "gb_profile_work": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64)]),
+    "gb_profile_kernels": (c_int, [c_void_p, POINTER(c_uint64)]),
     "gb_bitset_bytes": (c_uint64, [c_uint64]),
     "gb_strerror": (c_char_p, [c_int]),
     "gb_last_error": (c_char_p, []),
@@ -237,6 +242,37 @@ def gb_profile_work(ctx: int) -> dict:
     return dict(sieve_strikes=a.value, cover_iterations=b.value)
 
 
+GB_TUNE_PLAIN, GB_TUNE_BATCH = 0, 1
+
+
+def gb_set_config(ctx: int, **fields) -> dict:
+    """Change tunable configuration fields (see gb.h); returns the new config."""
+    c = gb_config()
+    _check(load().gb_get_config(ctx, ctypes.byref(c)), "gb_get_config")
+    for k, v in fields.items():
+        setattr(c, k, v)
+    _check(load().gb_set_config(ctx, ctypes.byref(c)), "gb_set_config")
+    return gb_get_config(ctx)
+
+
+def gb_autotune(ctx: int, ranges, mode: int = GB_TUNE_BATCH, reps: int = 2):
+    """Tune the context on a sample workload [(lo, hi), ...]; returns
+    (config dict, best ms)."""
+    count = len(ranges)
+    lo = (c_uint64 * count)(*[int(a) for a, _ in ranges])
+    hi = (c_uint64 * count)(*[int(b) for _, b in ranges])
+    c = gb_config()
+    ms = ctypes.c_double()
+    _check(load().gb_autotune(ctx, lo, hi, count, mode, reps, ctypes.byref(c), ctypes.byref(ms)), "gb_autotune")
+    return {f: getattr(c, f) for f, _ in gb_config._fields_}, ms.value
+
+
+def gb_profile_kernels(ctx: int) -> int:
+    n = c_uint64()
+    _check(load().gb_profile_kernels(ctx, ctypes.byref(n)), "gb_profile_kernels")
+    return n.value
+
+
 def gb_verify_batch(ctx: int, ranges, P: int = 0, *, hist_stride: int = 0, results=None, hist=None,
                     allow_erange: bool = False) -> dict:
     """Verify many ranges [(lo, hi), ...] in one batched pass.  Returns a dict
@@ -323,3 +359,9 @@ class Context:
 
     def verify_batch(self, ranges, P=0, **kw):
         return gb_verify_batch(self.handle, ranges, P, **kw)
+
+    def set_config(self, **fields):
+        return gb_set_config(self.handle, **fields)
+
+    def autotune(self, ranges, mode=GB_TUNE_BATCH, reps=2):
+        return gb_autotune(self.handle, ranges, mode, reps)

@@ -130,3 +130,50 @@ def test_batch_4096_ranges_sampled(ctx, oracle):
     short = [i for i, (lo, hi) in enumerate(ranges) if (hi - lo) // 2 <= (1 << 18)]
     pick = [short[k] for k in sample_indices(len(short), 12, seed=3)]
     _check_vs_oracle(oracle, [ranges[i] for i in pick], {"records": [out["records"][i] for i in pick]}, 0)
+
+
+def test_set_config_and_autotune(gbm):
+    from paper_2603_02621_gb300.workloads import batched_ranges
+    ranges = batched_ranges(count=64, seed=2, log2_min=10, log2_max=18, start_min=10**9, start_max=10**13)
+    with gbm.Context(device=0, base_limit=1 << 26, seg_len=1 << 20, p1=P1, p2=P2) as g:
+        before = g.verify_batch(ranges, hist_stride=512)
+        plain_before = [g.verify_range(lo, hi, hist_cap=512) for lo, hi in ranges[:3]]
+        with pytest.raises(RuntimeError):
+            g.set_config(base_limit=1 << 20)
+        with pytest.raises(RuntimeError):
+            g.set_config(cover_prefix=100)
+        cfg = g.set_config(tile_bits=1 << 16, bucket_split=1 << 15, cover_prefix=64, p1=1 << 12)
+        assert (cfg["tile_bits"], cfg["bucket_split"], cfg["cover_prefix"], cfg["p1"]) == (1 << 16, 1 << 15, 64, 1 << 12)
+        cfg, ms = g.autotune(ranges, gbm.GB_TUNE_BATCH, reps=1)
+        assert ms > 0 and g.config() == cfg
+        after = g.verify_batch(ranges, hist_stride=512)
+        assert after["records"] == before["records"]
+        np.testing.assert_array_equal(after["hist"], before["hist"])
+        cfg, ms = g.autotune(ranges[:3], gbm.GB_TUNE_PLAIN, reps=1)
+        assert ms > 0
+        for (lo, hi), ref in zip(ranges[:3], plain_before):
+            got = g.verify_range(lo, hi, hist_cap=512)
+            for k in ("n_checked", "unresolved", "max_pmin", "max_pmin_n", "hist_len"):
+                assert got[k] == ref[k]
+            np.testing.assert_array_equal(got["hist"], ref["hist"])
+
+
+def test_batch_graph_and_plain_launches_agree(gbm, monkeypatch):
+    """The batch kernels captured as a CUDA graph (default) and launched one
+    by one (GB_BATCH_GRAPH=0) give the same outputs; repeated calls re-use
+    the graph by update."""
+    from paper_2603_02621_gb300.workloads import batched_ranges
+    ranges = batched_ranges(count=200, seed=9, log2_min=4, log2_max=19, start_min=10**9, start_max=10**14)
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GB_BATCH_GRAPH", flag)
+        with gbm.Context(device=0, base_limit=1 << 24, seg_len=1 << 20, p1=P1, p2=P2) as g:
+            a = g.verify_batch(ranges, hist_stride=600)
+            b = g.verify_batch(ranges[::-1], hist_stride=600)
+            c = g.verify_batch(ranges, hist_stride=600)
+            assert a["records"] == c["records"] and a["records"] == b["records"][::-1]
+            np.testing.assert_array_equal(a["hist"], c["hist"])
+            np.testing.assert_array_equal(a["hist"], b["hist"][::-1])
+            outs.append(a)
+    assert outs[0]["records"] == outs[1]["records"]
+    np.testing.assert_array_equal(outs[0]["hist"], outs[1]["hist"])
