@@ -194,6 +194,20 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P,
 int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_t count, uint32_t P,
                     gb_segment_result* results, uint64_t* hist, uint32_t hist_stride);
 
+/* Single-n query (Sec. 2.4, the single-number check; here the minimal p):
+ * *p_min = the smallest prime p <= P with n - p prime, 0 if there is none,
+ * for even n with 4 <= n < 2^63 (GB_EINVAL otherwise).  P is the context's
+ * larger bound max(p1, p2).  Computed on the GPU: a window pre-sieve of the
+ * partners n - p by the primes <= 2048, then a deterministic Miller-Rabin test
+ * (bases 2..37) of each surviving partner, in ascending p.  Synchronous. */
+int gb_query(gb_ctx* ctx, uint64_t n, uint32_t* p_min);
+
+/* count queries at once (one CTA per n): n and p_min are host or device
+ * arrays of count entries; P as for gb_verify_range's bound (0: the context's
+ * max(p1, p2)), at most the base primes.  Any invalid n gives GB_EINVAL (its
+ * p_min is 0; the others are still computed).  Synchronous. */
+int gb_query_batch(gb_ctx* ctx, const uint64_t* n, uint32_t count, uint32_t P, uint32_t* p_min);
+
 /* gb_verify_range without memory allocation (the paper has no counterpart:
  * this is a calling convention of this library).  Some callers must not call
  * cudaMalloc while they run -- it can synchronize the device and stall every

@@ -139,6 +139,7 @@ struct gb_ctx {
     DevBuf work;                      // profiling work counters: [0] sieve strikes, [1] cover iterations
     // batched mode
     DevBuf bq, bhist, bkeys, bunres, bdesc, brecords, brows;
+    DevBuf qn, qout;                  // single-n queries: inputs, outputs + invalid-n counter
     HostBuf hstage;
     bool batch_graph = true;          // batch kernels as one CUDA graph (GB_BATCH_GRAPH=0: plain launches)
     bool capturing = false;           // cap_stream is being captured (profiling events become graph nodes)
@@ -486,7 +487,8 @@ void gb_destroy(gb_ctx* ctx)
     DevBuf* bufs[] = {&ctx->primes, &ctx->recip, &ctx->wheel, &ctx->q, &ctx->hist,
                       &ctx->maxkey, &ctx->maxkey2, &ctx->unres, &ctx->retry, &ctx->retry_count, &ctx->summary,
                       &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work,
-                      &ctx->bq, &ctx->bhist, &ctx->bkeys, &ctx->bunres, &ctx->bdesc, &ctx->brecords, &ctx->brows};
+                      &ctx->bq, &ctx->bhist, &ctx->bkeys, &ctx->bunres, &ctx->bdesc, &ctx->brecords, &ctx->brows,
+                      &ctx->qn, &ctx->qout};
     for (DevBuf* b : bufs) b->release();
     delete ctx;
 }
@@ -1073,6 +1075,54 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     if (!res_dev) std::memcpy(results, rec.data(), (size_t)count * sizeof(gb::SegRecord));
     if (status == GB_ERANGE) return fail(GB_ERANGE, "a histogram row was longer than hist_stride");
     return GB_OK;
+}
+
+int gb_query_batch(gb_ctx* ctx, const uint64_t* n, uint32_t count, uint32_t P, uint32_t* p_min)
+{
+    if (!ctx || (count && (!n || !p_min))) return fail(GB_EINVAL, "NULL argument");
+    if (count == 0) return GB_OK;
+    const gb_config& cfg = ctx->cfg;
+    const uint32_t Pq = P ? P : std::max(cfg.p1, cfg.p2);
+    if (Pq < 3 || Pq > ctx->L) return fail(GB_EINVAL, "P must be in [3, base primes]");
+    if (ctx->L < gb::query_filter_max()) return fail(GB_EINVAL, "queries need base primes to 2048");
+    GB_CUDA(cudaSetDevice(cfg.device));
+    cudaStream_t s = ctx->stream;
+    const bool n_dev = is_device_ptr(n), out_dev = is_device_ptr(p_min);
+    if (!n_dev)
+        for (uint32_t i = 0; i < count; ++i)
+            if ((n[i] & 1) || n[i] < 4 || n[i] >= (1ull << 63)) return fail(GB_EINVAL, "n must be even, 4 <= n < 2^63");
+    int rc;
+    if ((!n_dev && (rc = ctx->qn.ensure((size_t)count * 8))) || (rc = ctx->qout.ensure((size_t)count * 4 + 16)))
+        return rc;
+    const uint64_t* d_n = n;
+    if (!n_dev) {
+        GB_CUDA(cudaMemcpyAsync(ctx->qn.p, n, (size_t)count * 8, cudaMemcpyHostToDevice, s));
+        d_n = ctx->qn.as<uint64_t>();
+    }
+    unsigned int* bad = reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(ctx->qout.p) + (size_t)count * 4);
+    GB_CUDA(cudaMemsetAsync(bad, 0, 4, s));
+    gb::QueryArgs qa{};
+    qa.n = d_n;
+    qa.count = count;
+    qa.primes = ctx->primes.as<uint32_t>();
+    qa.recip = ctx->recip.as<uint64_t>();
+    qa.n_filter = (uint32_t)(ctx->pi(gb::query_filter_max()) - 1);
+    qa.K = (uint32_t)(ctx->pi(Pq) - 1);
+    qa.out = out_dev ? p_min : ctx->qout.as<uint32_t>();
+    qa.bad = bad;
+    GB_LAUNCH(gb::launch_query(qa, s));
+    unsigned int h_bad = 0;
+    GB_CUDA(cudaMemcpyAsync(&h_bad, bad, 4, cudaMemcpyDeviceToHost, s));
+    if (!out_dev) GB_CUDA(cudaMemcpyAsync(p_min, qa.out, (size_t)count * 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (h_bad) return fail(GB_EINVAL, "n must be even, 4 <= n < 2^63 (device input)");
+    return GB_OK;
+}
+
+int gb_query(gb_ctx* ctx, uint64_t n, uint32_t* p_min)
+{
+    if (!ctx || !p_min) return fail(GB_EINVAL, "NULL argument");
+    return gb_query_batch(ctx, &n, 1, 0, p_min);
 }
 
 int gb_profile_enable(gb_ctx* ctx, int enable)

@@ -283,6 +283,20 @@ struct ReduceBatchArgs {
 };
 cudaError_t launch_reduce_batch(const ReduceBatchArgs& a, uint32_t grid, cudaStream_t s);
 
+// Single-n queries (gb_query.cu): one CTA per n, p_min over primes[1..K]
+struct QueryArgs {
+    const uint64_t* n;          // device: even n, 4 <= n < 2^63
+    uint32_t count;
+    const uint32_t* primes;     // [2, 3, 5, ...]
+    const uint64_t* recip;
+    uint32_t n_filter;          // pre-sieve primes primes[1..n_filter] (all odd primes <= query_filter_max())
+    uint32_t K;                 // candidates primes[1..K] (p <= P)
+    uint32_t* out;              // device: p_min, 0 if no p <= P
+    unsigned int* bad;          // device: count of invalid n (their out is 0)
+};
+cudaError_t launch_query(const QueryArgs& a, cudaStream_t s);
+uint32_t query_filter_max();
+
 // Read-only view of a context for entry points defined outside gb_api.cu.
 struct CtxView {
     int device;

@@ -62,6 +62,8 @@ SIGNATURES = {
     "gb_verify_range_noalloc": (c_int, [c_void_p, c_uint64, c_uint64, c_uint32, POINTER(gb_range_result)]),
     "gb_verify_batch": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), c_uint32, c_uint32,
                                 c_void_p, c_void_p, c_uint32]),
+    "gb_query": (c_int, [c_void_p, c_uint64, POINTER(c_uint32)]),
+    "gb_query_batch": (c_int, [c_void_p, c_void_p, c_uint32, c_uint32, c_void_p]),
     "gb_set_config": (c_int, [c_void_p, POINTER(gb_config)]),
     "gb_autotune": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), c_uint32, c_int, c_uint32,
                             POINTER(gb_config), POINTER(ctypes.c_double)]),
@@ -242,6 +244,35 @@ def gb_profile_work(ctx: int) -> dict:
     return dict(sieve_strikes=a.value, cover_iterations=b.value)
 
 
+def gb_query(ctx: int, n: int) -> int:
+    """p_min(n) (0 if no p <= the context's bound), computed on the GPU."""
+    out = c_uint32()
+    _check(load().gb_query(ctx, int(n), ctypes.byref(out)), "gb_query")
+    return out.value
+
+
+def gb_query_batch(ctx: int, ns, P: int = 0, *, out=None, allow_einval: bool = False):
+    """p_min for many n: ns is a sequence / numpy array (host) or a CUDA
+    tensor of int64 (device); out (optional) a CUDA int32 tensor.  Returns a
+    numpy uint32 array for host output."""
+    lib = load()
+    if hasattr(ns, "data_ptr"):
+        n_ptr, count = ns.data_ptr(), ns.numel()
+        keep = None
+    else:
+        keep = np.ascontiguousarray(np.asarray(ns, dtype=np.uint64))
+        n_ptr, count = int(keep.ctypes.data), keep.size
+    res = None
+    if out is None:
+        res = np.zeros(count, dtype=np.uint32)
+        o_ptr = int(res.ctypes.data)
+    else:
+        o_ptr = out.data_ptr()
+    _check(lib.gb_query_batch(ctx, n_ptr, count, P, o_ptr), "gb_query_batch",
+           allow=(GB_EINVAL,) if allow_einval else ())
+    return res
+
+
 GB_TUNE_PLAIN, GB_TUNE_BATCH = 0, 1
 
 
@@ -359,6 +390,12 @@ class Context:
 
     def verify_batch(self, ranges, P=0, **kw):
         return gb_verify_batch(self.handle, ranges, P, **kw)
+
+    def query(self, n):
+        return gb_query(self.handle, n)
+
+    def query_batch(self, ns, P=0, **kw):
+        return gb_query_batch(self.handle, ns, P, **kw)
 
     def set_config(self, **fields):
         return gb_set_config(self.handle, **fields)
