@@ -65,6 +65,10 @@ def base_for(mode: str, hi: int) -> int:
 
 
 def workload_desc(mode: str, world: int):
+    if mode == "serving":
+        return {"workload": "serving: Poisson stream, 2000 req/s offered, 90% ranges of 2^16..2^30 even n "
+                            "at offsets uniform in [1e9, 4e18], 10% single-n queries (n < 4e18)",
+                "requests": 2000, "seed": 7, "p2": P2}
     if mode == "batched":
         return {"workload": "4096 ranges per GPU, lengths log-uniform 2^10..2^26 even n, starts uniform "
                             "in [1e9, 1e15] (splitmix64 seed 1 + rank), one gb_verify_batch call",
@@ -172,6 +176,8 @@ def sample_units(mode: str, seed: int = 11):
     from paper_2603_02621_gb300 import workloads
     if mode == "batched":
         units = workloads.batched_ranges(count=4096, seed=1)
+    elif mode == "serving":
+        units = [(a, b) for t, kind, a, b in workloads.serving_stream(count=2000, seed=7) if kind == "range"]
     else:
         lo, hi = rank_range(mode, 0)
         seg = PLAIN_MODES[mode]["seg"]
@@ -209,7 +215,8 @@ def cpu_baseline(mode: str = "plain", min_seconds: float = 12.0, seed: int = 11)
             done_n += sum(ex.map(one, batch))
             used += len(batch)
     dt = time.perf_counter() - t0
-    kind = "ranges of the 4096-range batch" if mode == "batched" else "segments of " + mode
+    kind = {"batched": "ranges of the 4096-range batch", "serving": "range requests of the serving stream"}.get(
+        mode, "segments of " + mode)
     return {"value": done_n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{used} seeded {kind} ({done_n} n, {dt:.1f} s wall, P = 2^20)",
             "seconds": dt}
@@ -242,6 +249,10 @@ def run_reference(args, world, rank):
 
 
 def workload_n(mode: str, rank: int = 0) -> int:
+    if mode == "serving":
+        from paper_2603_02621_gb300 import workloads
+        return sum((b - a) // 2 for t, kind, a, b in workloads.serving_stream(count=2000, seed=7 + rank)
+                   if kind == "range")
     if mode == "batched":
         from paper_2603_02621_gb300 import workloads
         return sum((b - a) // 2 for a, b in workloads.batched_ranges(count=4096, seed=1 + rank))
@@ -376,6 +387,87 @@ class BatchWork:
                 "autotune_best_ms": self.tune_ms}
 
 
+# ----------------------------------------------------------------------------- serving
+def run_serving(args, gb, torch, world, rank, local, backend_ready):
+    """Config-5 style serving: a Poisson stream (2000 req/s offered, seed 7 +
+    rank) of 90% range verifications (2^16..2^30 even n at offsets uniform in
+    [1e9, 4e18]) and 10% single-n queries, paced by arrival time into the
+    continuous-batching server; value = range n verified per second of wall
+    time from the first arrival to the last completion."""
+    from paper_2603_02621_gb300 import workloads
+    ctx = gb.Context(device=local, base_limit=1 << 32, p1=P1, p2=P2)
+
+    def serve(reqs, lanes):
+        out = [None] * len(reqs)
+        with gb.Server(ctx, lanes=lanes, hbm_budget=args.hbm_budget << 30, max_batch=256) as srv:
+            tickets = [None] * len(reqs)
+
+            def submitter():
+                t0 = time.perf_counter()
+                for i, (t, kind, a, b) in enumerate(reqs):
+                    dt = t - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                    tickets[i] = srv.submit(kind, a, b)
+            th = threading.Thread(target=submitter)
+            w0 = time.perf_counter()
+            th.start()
+            for i in range(len(reqs)):
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                out[i] = srv.wait(tickets[i])
+            th.join()
+            wall = time.perf_counter() - w0
+            st = srv.stats()
+        return out, wall, st
+
+    serve(workloads.serving_stream(count=200, seed=1000 + rank), args.lanes)       # warm-up, arenas
+    reqs = workloads.serving_stream(count=args.requests, seed=7 + rank)
+    clocks = ClockSampler(local)
+    barrier(world, backend_ready)
+    clocks.start()
+    out, wall, st = serve(reqs, args.lanes)
+    clk = clocks.stop()
+    barrier(world, backend_ready)
+    bad = [r for r in out if r["status"] != 0]
+    first = min(r["t_submit_us"] for r in out)
+    last = max(r["t_done_us"] for r in out)
+    span_s = (last - first) / 1e6
+    span_s = reduce_max(span_s, world, backend_ready)
+    n_range = sum((b - a) // 2 for t, kind, a, b in reqs if kind == "range")
+    lat = {k: [] for k in ("range", "query")}
+    for (t, kind, a, b), r in zip(reqs, out):
+        lat[kind].append((r["t_done_us"] - r["t_submit_us"]) / 1000.0)
+    allv = sorted(lat["range"] + lat["query"])
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(q * len(v)))] if v else None
+
+    value = n_range * world / span_s
+    n_q = sum(1 for r in reqs if r[1] == "query")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": span_s * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic", "mode": "serving",
+            "config": {"workload": "serving: Poisson stream, 2000 req/s offered, 90% ranges of 2^16..2^30 even n "
+                                   "at offsets uniform in [1e9, 4e18], 10% single-n queries (n < 4e18)",
+                       "requests": len(reqs), "seed": 7, "lanes": args.lanes, "hbm_budget_gib": args.hbm_budget,
+                       "base_primes_to": 1 << 32, "p1": P1, "p2": P2,
+                       "offered_n_per_s": n_range / reqs[-1][0]},
+            "latency_ms": {"p50": pct(allv, 0.5), "p99": pct(allv, 0.99),
+                           "range_p50": pct(lat["range"], 0.5), "range_p99": pct(lat["range"], 0.99),
+                           "query_p50": pct(lat["query"], 0.5), "query_p99": pct(lat["query"], 0.99)},
+            "roofline": None,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 16 * (len(reqs) - n_q) + 8 * n_q,
+                    "d2h_bytes_per_step": 48 * (len(reqs) - n_q) + 4 * n_q},
+            "clocks": clk, "gpu_launches": None, "server": st, "failed_requests": len(bad),
+            "wall_s": wall, "paper_context": PAPER_CONTEXT}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -383,7 +475,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="plain", choices=sorted(PLAIN_MODES) + ["batched"])
+    ap.add_argument("--mode", default="plain", choices=sorted(PLAIN_MODES) + ["batched", "serving"])
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the timed stream")
+    ap.add_argument("--lanes", type=int, default=4, help="serving: server lanes")
+    ap.add_argument("--hbm-budget", type=int, default=64, help="serving: admission budget, GiB")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lo", type=int, default=None, help="custom range start (profiling of smaller cases)")
     ap.add_argument("--hi", type=int, default=None, help="custom range end")
@@ -402,6 +497,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         backend_ready = True
     stream = torch.cuda.current_stream()
+    if args.mode == "serving":
+        return run_serving(args, gb, torch, world, rank, local, backend_ready)
     if args.mode == "batched":
         work = BatchWork(gb, torch, args.mode, rank, local, stream)
     else:

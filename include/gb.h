@@ -128,6 +128,14 @@ typedef struct gb_range_result {
 int gb_init(gb_ctx** out, const gb_config* cfg);
 
 /* Release every device resource of the context (NULL is a no-op). */
+/* A second context on the same device that shares parent's base primes (no
+ * second base sieve, no second copy in device or host memory) but has its own
+ * stream (cudaStream_t, NULL = legacy default stream), its own device arenas
+ * and a copy of parent's tunable configuration: contexts made this way run
+ * their calls concurrently, one host thread each.  The shared primes live
+ * until the last context using them is destroyed. */
+int gb_init_shared(gb_ctx** out, const gb_ctx* parent, void* stream);
+
 void gb_destroy(gb_ctx* ctx);
 
 /* The configuration in effect, defaults filled in. */
@@ -207,6 +215,44 @@ int gb_query(gb_ctx* ctx, uint64_t n, uint32_t* p_min);
  * max(p1, p2)), at most the base primes.  Any invalid n gives GB_EINVAL (its
  * p_min is 0; the others are still computed).  Synchronous. */
 int gb_query_batch(gb_ctx* ctx, const uint64_t* n, uint32_t count, uint32_t P, uint32_t* p_min);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop with continuous batching.  The server owns `lanes` contexts
+ * made from ctx by gb_init_shared (shared base primes, one stream each), each
+ * driven by a host thread.  A free lane admits the requests at the head of
+ * the FIFO queue that fit in the free part of the device-memory budget (at
+ * most max_batch; a request larger than the whole budget runs alone) and runs
+ * them as one gb_verify_batch call and one gb_query_batch call; requests that
+ * arrive meanwhile are admitted by the next free lane, so their work overlaps
+ * on the GPU.  Results do not depend on the batching.  ctx must outlive the
+ * server and must not be used while the server runs. */
+#define GB_REQ_RANGE 0   /* verify every even n in [lo, hi) (at most 2^32 n) */
+#define GB_REQ_QUERY 1   /* p_min(n) for n = lo */
+typedef struct gb_request {
+    uint32_t kind;
+    uint32_t reserved;
+    uint64_t lo, hi;
+} gb_request;
+typedef struct gb_response {
+    int32_t status;             /* GB_OK or the error of the call that served it */
+    uint32_t p_min;             /* GB_REQ_QUERY: p_min(n), 0 if none <= P */
+    gb_segment_result range;    /* GB_REQ_RANGE: the range's record */
+    double t_submit_us;         /* host steady clock, microseconds since the */
+    double t_start_us;          /* server was created: submitted, its batch */
+    double t_done_us;           /* started, its batch finished */
+} gb_response;
+typedef struct gb_server gb_server;
+/* lanes 1..16; hbm_budget_bytes 0 = 8 GiB; max_batch 0 = 256 */
+int gb_server_create(gb_server** out, gb_ctx* ctx, uint32_t lanes, uint64_t hbm_budget_bytes, uint32_t max_batch);
+/* queue a request (GB_EINVAL if it is malformed or beyond base_limit^2) */
+int gb_server_submit(gb_server* srv, const gb_request* req, uint64_t* ticket);
+/* wait for a ticket's response (each ticket can be collected once);
+ * GB_ETIMEOUT if it is not done within timeout_ms */
+int gb_server_wait(gb_server* srv, uint64_t ticket, gb_response* out, uint32_t timeout_ms);
+int gb_server_stats(gb_server* srv, uint64_t* submitted, uint64_t* completed, uint64_t* batches,
+                    uint64_t* in_flight_max_bytes);
+/* finishes every queued request, then stops the lanes */
+void gb_server_destroy(gb_server* srv);
 
 /* gb_verify_range without memory allocation (the paper has no counterpart:
  * this is a calling convention of this library).  Some callers must not call

@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "gb.h"
@@ -127,13 +128,19 @@ uint64_t isqrt_u64(uint64_t x)
 
 }  // namespace
 
+// base primes: built once by gb_init, shared with the contexts made from it
+// by gb_init_shared (freed with the last of them)
+struct BasePrimes {
+    std::vector<uint32_t> h_primes;   // [2, 3, 5, ...] <= L
+    DevBuf primes, recip;             // device copies
+    DevBuf wheel;                     // pre-sieve stamp tables
+};
+
 struct gb_ctx {
     gb_config cfg{};
     cudaStream_t stream = nullptr;
     uint64_t L = 0;                   // primes are known up to L
-    std::vector<uint32_t> h_primes;   // [2, 3, 5, ...] <= L
-    DevBuf primes, recip;             // device copies
-    DevBuf wheel;                     // pre-sieve stamp tables
+    std::shared_ptr<BasePrimes> base = std::make_shared<BasePrimes>();
     DevBuf q;                         // slab q window
     DevBuf hist, maxkey, maxkey2, unres, retry, retry_count, summary, rows, merged, pmin, counter, totals, records;
     DevBuf work;                      // profiling work counters: [0] sieve strikes, [1] cover iterations
@@ -222,7 +229,7 @@ struct gb_ctx {
     // number of primes <= x (x <= L)
     uint64_t pi(uint64_t x) const
     {
-        return (uint64_t)(std::upper_bound(h_primes.begin(), h_primes.end(), (uint32_t)std::min<uint64_t>(x, 0xffffffffull)) - h_primes.begin());
+        return (uint64_t)(std::upper_bound(base->h_primes.begin(), base->h_primes.end(), (uint32_t)std::min<uint64_t>(x, 0xffffffffull)) - base->h_primes.begin());
     }
 };
 
@@ -271,14 +278,14 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
     a.B = B;
     a.nbits = nbits;
     a.tile_bits = ctx->cfg.tile_bits;
-    a.primes = ctx->primes.as<uint32_t>() + gb::kFirstStrikeIdx;
-    a.recip = ctx->recip.as<uint64_t>() + gb::kFirstStrikeIdx;
+    a.primes = ctx->base->primes.as<uint32_t>() + gb::kFirstStrikeIdx;
+    a.recip = ctx->base->recip.as<uint64_t>() + gb::kFirstStrikeIdx;
     const uint64_t nstrike = nsmall > gb::kFirstStrikeIdx ? nsmall - gb::kFirstStrikeIdx : 0;
     const uint64_t nwarp = std::min<uint64_t>(nstrike, ctx->pi((uint64_t)ctx->warp_split - 1) > gb::kFirstStrikeIdx
                                                             ? ctx->pi((uint64_t)ctx->warp_split - 1) - gb::kFirstStrikeIdx : 0);
     a.n_warp = (uint32_t)nwarp;
     a.n_primes = (uint32_t)nstrike;
-    a.wheel = ctx->wheel.as<uint32_t>();
+    a.wheel = ctx->base->wheel.as<uint32_t>();
     a.out = out;
     a.popcount = large ? nullptr : popc;
     a.strikes = ctx->work_ptr(0);
@@ -286,8 +293,8 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
     if (large) {
         gb::LargeArgs la{};
         la.B = B;
-        la.primes = ctx->primes.as<uint32_t>() + nsmall;
-        la.recip = ctx->recip.as<uint64_t>() + nsmall;
+        la.primes = ctx->base->primes.as<uint32_t>() + nsmall;
+        la.recip = ctx->base->recip.as<uint64_t>() + nsmall;
         la.n_primes = (uint32_t)(np - nsmall);
         la.out = out;
         la.strikes = ctx->work_ptr(0);
@@ -306,8 +313,8 @@ int build_primes(gb_ctx* ctx)
 {
     cudaStream_t s = ctx->stream;
     int rc;
-    if ((rc = ctx->wheel.ensure(gb::kWheelWords * 4))) return rc;
-    GB_CUDA(gb::launch_wheel_tables(ctx->wheel.as<uint32_t>(), s));
+    if ((rc = ctx->base->wheel.ensure(gb::kWheelWords * 4))) return rc;
+    GB_CUDA(gb::launch_wheel_tables(ctx->base->wheel.as<uint32_t>(), s));
 
     // seed: odd numbers 1 .. 65535
     DevBuf seedbits, counts, seedp, seedr;
@@ -331,20 +338,20 @@ int build_primes(gb_ctx* ctx)
 
     if (ctx->L <= 65535) {
         // the seed list already holds every prime <= L
-        ctx->h_primes.assign(seed.begin(), seed.end());
-        ctx->h_primes.resize(std::upper_bound(seed.begin(), seed.end(), (uint32_t)ctx->L) - seed.begin());
-        const size_t n = ctx->h_primes.size();
-        if ((rc = ctx->primes.ensure(n * 4)) || (rc = ctx->recip.ensure(n * 8))) return rc;
-        GB_CUDA(cudaMemcpyAsync(ctx->primes.p, seedp.p, n * 4, cudaMemcpyDeviceToDevice, s));
-        GB_CUDA(cudaMemcpyAsync(ctx->recip.p, seedr.p, n * 8, cudaMemcpyDeviceToDevice, s));
+        ctx->base->h_primes.assign(seed.begin(), seed.end());
+        ctx->base->h_primes.resize(std::upper_bound(seed.begin(), seed.end(), (uint32_t)ctx->L) - seed.begin());
+        const size_t n = ctx->base->h_primes.size();
+        if ((rc = ctx->base->primes.ensure(n * 4)) || (rc = ctx->base->recip.ensure(n * 8))) return rc;
+        GB_CUDA(cudaMemcpyAsync(ctx->base->primes.p, seedp.p, n * 4, cudaMemcpyDeviceToDevice, s));
+        GB_CUDA(cudaMemcpyAsync(ctx->base->recip.p, seedr.p, n * 8, cudaMemcpyDeviceToDevice, s));
         GB_CUDA(cudaStreamSynchronize(s));
         return GB_OK;
     }
 
     // base sieve of the odd numbers 1 .. L with the seed primes
-    ctx->h_primes = seed;                            // primes < 2^16 serve as sieving primes
-    ctx->primes.take(seedp);
-    ctx->recip.take(seedr);
+    ctx->base->h_primes = seed;                            // primes < 2^16 serve as sieving primes
+    ctx->base->primes.take(seedp);
+    ctx->base->recip.take(seedr);
     const uint64_t nbits = (ctx->L + 1) / 2;
     const uint64_t nwords = ((nbits + 63) / 64) * 2;
     DevBuf bits, popc;
@@ -360,11 +367,11 @@ int build_primes(gb_ctx* ctx)
     if ((rc = np.ensure(n * 4)) || (rc = nr.ensure(n * 8))) return rc;
     gb::CompactArgs cb{bits.as<uint32_t>(), nwords, 1, counts.as<uint32_t>(), np.as<uint32_t>(), nr.as<uint64_t>()};
     GB_CUDA(gb::launch_compact(cb, s));
-    ctx->h_primes.resize(n);
-    GB_CUDA(cudaMemcpyAsync(ctx->h_primes.data(), np.p, n * 4, cudaMemcpyDeviceToHost, s));
+    ctx->base->h_primes.resize(n);
+    GB_CUDA(cudaMemcpyAsync(ctx->base->h_primes.data(), np.p, n * 4, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
-    ctx->primes.take(np);
-    ctx->recip.take(nr);
+    ctx->base->primes.take(np);
+    ctx->base->recip.take(nr);
     return GB_OK;
 }
 
@@ -385,9 +392,9 @@ int ctx_view(const gb_ctx* ctx, CtxView* v)
     v->tile_bits = ctx->cfg.tile_bits;
     v->bucket_split = ctx->cfg.bucket_split;
     v->warp_split = (uint32_t)ctx->warp_split;
-    v->primes = ctx->primes.as<uint32_t>();
-    v->recip = ctx->recip.as<uint64_t>();
-    v->wheel = ctx->wheel.as<uint32_t>();
+    v->primes = ctx->base->primes.as<uint32_t>();
+    v->recip = ctx->base->recip.as<uint64_t>();
+    v->wheel = ctx->base->wheel.as<uint32_t>();
     v->generic_cover = ctx->generic_cover;
     v->ka_override = (int)ctx->cfg.cover_prefix;
     v->large_chunk_bits = ctx->large_chunk_bits;
@@ -478,13 +485,36 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     return GB_OK;
 }
 
+int gb_init_shared(gb_ctx** out, const gb_ctx* parent, void* stream)
+{
+    if (!out || !parent) return fail(GB_EINVAL, "NULL argument");
+    *out = nullptr;
+    GB_CUDA(cudaSetDevice(parent->cfg.device));
+    if (parent->stream) GB_CUDA(cudaStreamSynchronize(parent->stream));
+    else GB_CUDA(cudaDeviceSynchronize());
+    gb_ctx* ctx = new gb_ctx();
+    ctx->cfg = parent->cfg;
+    ctx->cfg.stream = stream;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->L = parent->L;
+    ctx->base = parent->base;
+    ctx->warp_split = parent->warp_split;
+    ctx->generic_cover = parent->generic_cover;
+    ctx->batch_graph = parent->batch_graph;
+    ctx->large_chunk_bits = parent->large_chunk_bits;
+    *out = ctx;
+    return GB_OK;
+}
+
 void gb_destroy(gb_ctx* ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->cfg.device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&ctx->primes, &ctx->recip, &ctx->wheel, &ctx->q, &ctx->hist,
+    // the base primes are shared with the contexts made by gb_init_shared:
+    // they are freed with the last context holding them (delete below)
+    DevBuf* bufs[] = {&ctx->q, &ctx->hist,
                       &ctx->maxkey, &ctx->maxkey2, &ctx->unres, &ctx->retry, &ctx->retry_count, &ctx->summary,
                       &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work,
                       &ctx->bq, &ctx->bhist, &ctx->bkeys, &ctx->bunres, &ctx->bdesc, &ctx->brecords, &ctx->brows,
@@ -660,7 +690,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         ca.cta_words = std::min<uint32_t>(2048, (uint32_t)(S / 64));
         ca.chunks_per_seg = (uint32_t)((S / 64 + ca.cta_words - 1) / ca.cta_words);
         ca.nseg = (uint32_t)ns;
-        ca.primes = ctx->primes.as<uint32_t>();
+        ca.primes = ctx->base->primes.as<uint32_t>();
         ca.K = K1;
         ca.hist_stride = hist_stride;
         ca.hist = ctx->hist.as<uint32_t>();
@@ -936,13 +966,13 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
         // sieve: tile part (persistent, item queue), then the large primes
         gb::SieveItemsArgs sa{};
         sa.base.tile_bits = T;
-        sa.base.primes = ctx->primes.as<uint32_t>() + gb::kFirstStrikeIdx;
-        sa.base.recip = ctx->recip.as<uint64_t>() + gb::kFirstStrikeIdx;
+        sa.base.primes = ctx->base->primes.as<uint32_t>() + gb::kFirstStrikeIdx;
+        sa.base.recip = ctx->base->recip.as<uint64_t>() + gb::kFirstStrikeIdx;
         const uint64_t nstrike = nsmall > gb::kFirstStrikeIdx ? nsmall - gb::kFirstStrikeIdx : 0;
         const uint64_t nwarp_all = ctx->pi((uint64_t)ctx->warp_split - 1);
         sa.base.n_warp = (uint32_t)std::min<uint64_t>(nstrike, nwarp_all > gb::kFirstStrikeIdx ? nwarp_all - gb::kFirstStrikeIdx : 0);
         sa.base.n_primes = (uint32_t)nstrike;
-        sa.base.wheel = ctx->wheel.as<uint32_t>();
+        sa.base.wheel = ctx->base->wheel.as<uint32_t>();
         sa.base.strikes = ctx->work_ptr(0);
         sa.ranges = d_ranges;
         sa.item_range = d_s_range;
@@ -958,8 +988,8 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
             la.groups = d_groups;
             la.n_items = d_counts + 3;
             la.head = heads + 2;
-            la.primes = ctx->primes.as<uint32_t>() + nsmall;
-            la.recip = ctx->recip.as<uint64_t>() + nsmall;
+            la.primes = ctx->base->primes.as<uint32_t>() + nsmall;
+            la.recip = ctx->base->recip.as<uint64_t>() + nsmall;
             la.n_primes = (uint32_t)(np - nsmall);
             la.Q = ctx->bq.as<uint32_t>();
             la.strikes = ctx->work_ptr(0);
@@ -972,7 +1002,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
         gb::CoverItemsArgs cv{};
         cv.base.H = H;
         cv.base.cta_words = cw;
-        cv.base.primes = ctx->primes.as<uint32_t>();
+        cv.base.primes = ctx->base->primes.as<uint32_t>();
         cv.base.K = K1;
         cv.base.hist_stride = hs;
         cv.base.hist = ctx->bhist.as<uint32_t>();
@@ -996,7 +1026,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
         ra.hist_stride = hs;
         ra.maxkey = ctx->bkeys.as<unsigned long long>();
         ra.unresolved = ctx->bunres.as<unsigned long long>();
-        ra.primes = ctx->primes.as<uint32_t>();
+        ra.primes = ctx->base->primes.as<uint32_t>();
         ra.records = d_records;
         ra.rows = want_rows ? (rows_dev ? hist : ctx->brows.as<uint64_t>()) : nullptr;
         ra.row_stride = want_rows ? hist_stride : 0;
@@ -1104,8 +1134,8 @@ int gb_query_batch(gb_ctx* ctx, const uint64_t* n, uint32_t count, uint32_t P, u
     gb::QueryArgs qa{};
     qa.n = d_n;
     qa.count = count;
-    qa.primes = ctx->primes.as<uint32_t>();
-    qa.recip = ctx->recip.as<uint64_t>();
+    qa.primes = ctx->base->primes.as<uint32_t>();
+    qa.recip = ctx->base->recip.as<uint64_t>();
     qa.n_filter = (uint32_t)(ctx->pi(gb::query_filter_max()) - 1);
     qa.K = (uint32_t)(ctx->pi(Pq) - 1);
     qa.out = out_dev ? p_min : ctx->qout.as<uint32_t>();

@@ -40,6 +40,18 @@ class gb_segment_result(ctypes.Structure):
                 ("max_pmin", c_uint32), ("hist_len", c_uint32)]
 
 
+class gb_request(ctypes.Structure):
+    _fields_ = [("kind", c_uint32), ("reserved", c_uint32), ("lo", c_uint64), ("hi", c_uint64)]
+
+
+class gb_response(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("p_min", c_uint32), ("range", gb_segment_result),
+                ("t_submit_us", ctypes.c_double), ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+GB_REQ_RANGE, GB_REQ_QUERY = 0, 1
+
+
 class gb_range_result(ctypes.Structure):
     _fields_ = [("n_checked", c_uint64), ("unresolved", c_uint64), ("max_pmin_n", c_uint64),
                 ("max_pmin", c_uint32), ("hist_len", c_uint32), ("n_segments", c_uint32),
@@ -65,6 +77,13 @@ SIGNATURES = {
     "gb_query": (c_int, [c_void_p, c_uint64, POINTER(c_uint32)]),
     "gb_query_batch": (c_int, [c_void_p, c_void_p, c_uint32, c_uint32, c_void_p]),
     "gb_set_config": (c_int, [c_void_p, POINTER(gb_config)]),
+    "gb_init_shared": (c_int, [POINTER(c_void_p), c_void_p, c_void_p]),
+    "gb_server_create": (c_int, [POINTER(c_void_p), c_void_p, c_uint32, c_uint64, c_uint32]),
+    "gb_server_submit": (c_int, [c_void_p, POINTER(gb_request), POINTER(c_uint64)]),
+    "gb_server_wait": (c_int, [c_void_p, c_uint64, POINTER(gb_response), c_uint32]),
+    "gb_server_stats": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), POINTER(c_uint64),
+                                POINTER(c_uint64)]),
+    "gb_server_destroy": (None, [c_void_p]),
     "gb_autotune": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), c_uint32, c_int, c_uint32,
                             POINTER(gb_config), POINTER(ctypes.c_double)]),
     "gb_profile_enable": (c_int, [c_void_p, c_int]),
@@ -353,8 +372,15 @@ def gb_last_error() -> str:
 class Context:
     """Owning wrapper: ``with Context(base_limit=10**5) as g: g.verify_range(...)``."""
 
-    def __init__(self, **cfg):
-        self.handle = gb_init(**cfg)
+    def __init__(self, _handle=None, **cfg):
+        self.handle = _handle if _handle is not None else gb_init(**cfg)
+
+    def share(self, stream: int = 0) -> "Context":
+        """A context sharing this one's base primes, with its own stream
+        (cudaStream_t as an int, 0 = legacy default) and arenas."""
+        h = c_void_p()
+        _check(load().gb_init_shared(ctypes.byref(h), self.handle, stream or None), "gb_init_shared")
+        return Context(_handle=h.value)
 
     def close(self):
         if self.handle:
@@ -402,3 +428,48 @@ class Context:
 
     def autotune(self, ranges, mode=GB_TUNE_BATCH, reps=2):
         return gb_autotune(self.handle, ranges, mode, reps)
+
+
+class Server:
+    """Request loop with continuous batching over `lanes` GPU lanes (gb.h,
+    serving).  submit() queues a range ('range', lo, hi) or a query
+    ('query', n) and returns a ticket; wait(ticket) returns its response."""
+
+    def __init__(self, ctx: "Context", lanes: int = 4, hbm_budget: int = 0, max_batch: int = 0):
+        self.ctx = ctx
+        h = c_void_p()
+        _check(load().gb_server_create(ctypes.byref(h), ctx.handle, lanes, hbm_budget, max_batch),
+               "gb_server_create")
+        self.handle = h.value
+
+    def submit(self, kind: str, a: int, b: int = 0) -> int:
+        r = gb_request(GB_REQ_RANGE if kind == "range" else GB_REQ_QUERY, 0, int(a), int(b))
+        t = c_uint64()
+        _check(load().gb_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "gb_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 600000) -> dict:
+        r = gb_response()
+        _check(load().gb_server_wait(self.handle, ticket, ctypes.byref(r), timeout_ms), "gb_server_wait")
+        g = r.range
+        return dict(status=r.status, p_min=r.p_min,
+                    range=dict(lo=g.lo, hi=g.hi, n_checked=g.n_checked, unresolved=g.unresolved,
+                               max_pmin=g.max_pmin, max_pmin_n=g.max_pmin_n, hist_len=g.hist_len),
+                    t_submit_us=r.t_submit_us, t_start_us=r.t_start_us, t_done_us=r.t_done_us)
+
+    def stats(self) -> dict:
+        v = [c_uint64() for _ in range(4)]
+        _check(load().gb_server_stats(self.handle, *[ctypes.byref(x) for x in v]), "gb_server_stats")
+        return dict(submitted=v[0].value, completed=v[1].value, batches=v[2].value,
+                    in_flight_max_bytes=v[3].value)
+
+    def close(self):
+        if self.handle:
+            load().gb_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
