@@ -281,6 +281,15 @@ class PlainWork:
         self.h2d = 0
         self.d2h = 32 + self.nseg * 48 + self.nseg * HL * 8 + HL * 8
         self.last = None
+        self.tuned = None
+
+    def autotune(self, torch):
+        """gb_autotune on the rank's own range (plain mode), before timing."""
+        cfg, ms = self.ctx.autotune([(self.lo, self.hi)], self.gb.GB_TUNE_PLAIN, reps=1)
+        # per-segment outputs follow seg_len: keep the workload's
+        self.ctx.set_config(seg_len=self.seg)
+        self.tuned = ({k: cfg[k] for k in ("tile_bits", "bucket_split", "cta_threads", "p1", "cover_prefix")},
+                      ms)
 
     def _call(self, rows, segs, hist):
         gb = self.gb
@@ -310,7 +319,9 @@ class PlainWork:
                 "max_pmin_n": int(r.max_pmin_n), "n_checked": int(r.n_checked)}
 
     def extra(self, args):
-        return {}
+        if self.tuned is None:
+            return {}
+        return {"autotuned": self.tuned[0], "autotune_best_ms": self.tuned[1]}
 
 
 class BatchWork:
@@ -480,6 +491,7 @@ def main():
     ap.add_argument("--lanes", type=int, default=4, help="serving: server lanes")
     ap.add_argument("--hbm-budget", type=int, default=64, help="serving: admission budget, GiB")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="plain family: run gb_autotune on the range first")
     ap.add_argument("--lo", type=int, default=None, help="custom range start (profiling of smaller cases)")
     ap.add_argument("--hi", type=int, default=None, help="custom range end")
     args = ap.parse_args()
@@ -505,6 +517,8 @@ def main():
         if args.lo is not None and args.hi is not None:
             PLAIN_MODES[args.mode].update(lo=args.lo, hi=args.hi, shift=args.hi - args.lo)
         work = PlainWork(gb, torch, args.mode, rank, local, stream)
+        if args.autotune:
+            work.autotune(torch)
     ctx = work.ctx
 
     for _ in range(args.warmup):
@@ -558,11 +572,18 @@ def main():
     # DRAM bytes per unit measured by ncu on [4, 2^32] (plain workload's kernels)
     ncu_traffic = {"cover": 0.1269, "sieve": 0.09657} if args.mode == "plain" else {}
     per = {}
-    for kern in ("sieve", "cover"):
+    for kern in ("sieve", "cover", "large"):
         kp = prof[kern]
-        nl = max(1, kp["launches"])
+        if kp["launches"] == 0:
+            continue
+        nl = kp["launches"]
         ms = kp["ms"] / nl
-        if kern == "cover":
+        if kern == "large":
+            # primes above the tile split: 2 ALU ops per strike (word index,
+            # rotated mask) issued as a global atomic AND
+            units = wk["large_strikes"] / nl
+            ops = 2.0 * units
+        elif kern == "cover":
             # minimal ALU work: 2 ops per (32-bit coverage word, prime) step,
             # the funnel shift that aligns the partner bits and the OR into C;
             # 2 per probed (n, prime): shift and bit test
@@ -576,11 +597,12 @@ def main():
         alg_bytes = kp["units"] / nl / 8.0               # the q bits, written once / read once
         traffic = ncu_traffic[kern] * kp["units"] / nl if kern in ncu_traffic else None
         achieved = ops / (ms / 1000.0) / 1e12
-        per[kern] = {"ms_per_launch": ms, "achieved": achieved, "frac": achieved / alu_peak,
+        per[kern] = {"ms_per_launch": ms, "ms_total": kp["ms"], "launches": nl,
+                     "achieved": achieved, "frac": achieved / alu_peak,
                      "alu_ops_per_launch": ops, "work_units_per_launch": units,
                      "dram_bytes_per_launch": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                      "hbm_frac": (alg_bytes / (ms / 1000.0)) / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)}
-    kern = max(per, key=lambda k: per[k]["ms_per_launch"])
+    kern = max(per, key=lambda k: per[k]["ms_total"])
     roofline = {"kernel": kern, "bound": "alu", "achieved": per[kern]["achieved"], "peak": alu_peak,
                 "unit": "T ALU lane-ops/s", "frac": per[kern]["frac"],
                 "traffic": per[kern]["dram_bytes_per_launch"],

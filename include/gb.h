@@ -283,21 +283,24 @@ int gb_verify_range_noalloc(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P,
 
 /* Per-kernel device time, measured with CUDA events recorded on the
  * context's stream around every launch while profiling is enabled.  Kinds:
- * 0 segment sieve (units: q bits sieved), 1 cover (units: even n), 2 retry
- * pass (units: even n of the slabs it ran on), 3 reductions and the max-only
- * pass (units: segments).  gb_profile_enable resets the counters. */
-#define GB_PROF_KINDS 4
+ * 0 segment sieve, tile part (units: q bits sieved), 1 cover (units: even n;
+ * batched mode: q bits), 2 retry pass (units: even n of the slabs it ran on),
+ * 3 reductions and the max-only pass (units: segments), 4 segment sieve,
+ * primes above the tile split (units: q bits).  gb_profile_enable resets the
+ * counters. */
+#define GB_PROF_KINDS 5
 int gb_profile_enable(gb_ctx* ctx, int enable);
 int gb_profile_read(gb_ctx* ctx, double* ms, uint64_t* launches, uint64_t* units);
 
 /* Work counted by the kernels while profiling is enabled: bits struck by the
- * segment sieve (every strike of a prime >= 47, duplicates included; primes
- * 3..43 are stamped from patterns), and the cover's steps: for the two-phase
- * kernel, first-phase (32-bit word, prime) steps plus second-phase (n, prime)
- * probes; for the generic kernel, the sum over 64-n words of the number of
- * primes applied until the word filled (the bound's count for a word left
- * open). */
-int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterations);
+ * segment sieve's tile part (every strike of a prime >= 47 below the tile
+ * split, duplicates included; primes 3..43 are stamped from patterns); the
+ * cover's steps: for the two-phase kernel, first-phase (32-bit word, prime)
+ * steps plus second-phase (n, prime) probes; for the generic kernel, the sum
+ * over 64-n words of the number of primes applied until the word filled (the
+ * bound's count for a word left open); and the bits struck by the primes
+ * above the tile split. */
+int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterations, uint64_t* large_strikes);
 
 /* Kernels launched by verification calls of this context since the last
  * gb_profile_enable (counted whether or not profiling is on). */

@@ -24,7 +24,7 @@
 
 namespace {
 
-enum { kProfSieve = 0, kProfCover = 1, kProfRetry = 2, kProfReduce = 3 };
+enum { kProfSieve = 0, kProfCover = 1, kProfRetry = 2, kProfReduce = 3, kProfLarge = 4 };
 
 thread_local std::string g_last_error;
 
@@ -152,7 +152,7 @@ struct gb_ctx {
     bool capturing = false;           // cap_stream is being captured (profiling events become graph nodes)
     cudaStream_t cap_stream = nullptr;  // private stream the batch graph is captured on
     cudaGraphExec_t bgraph = nullptr;
-    uint64_t work_strikes = 0, work_iters = 0;
+    uint64_t work_strikes = 0, work_iters = 0, work_large = 0;
     int warp_split = 0;               // sieving primes below this strike one warp each
     bool generic_cover = false;       // force the generic cover kernel (GB_COVER=generic)
     uint64_t large_chunk_bits = 1ull << 28;   // large-prime strikes per L2-resident chunk of the window
@@ -199,12 +199,13 @@ struct gb_ctx {
     int prof_collect()
     {
         if (work.p) {
-            unsigned long long w[2] = {0, 0};
+            unsigned long long w[3] = {0, 0, 0};
             cudaError_t e = cudaMemcpy(w, work.p, sizeof w, cudaMemcpyDeviceToHost);
             if (e == cudaSuccess) e = cudaMemset(work.p, 0, sizeof w);
             if (e != cudaSuccess) return fail(GB_ECUDA, std::string("profile counters: ") + cudaGetErrorString(e));
             work_strikes += w[0];
             work_iters += w[1];
+            work_large += w[2];
         }
         for (const Pending& p : pending) {
             cudaError_t e = cudaEventSynchronize(p.b);
@@ -289,15 +290,18 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
     a.out = out;
     a.popcount = large ? nullptr : popc;
     a.strikes = ctx->work_ptr(0);
+    ctx->prof_begin(kProfSieve, nbits);
     GB_LAUNCH(gb::launch_sieve(a, (int)ctx->cfg.cta_threads, ctx->stream));
+    ctx->prof_end();
     if (large) {
+        ctx->prof_begin(kProfLarge, nbits);
         gb::LargeArgs la{};
         la.B = B;
         la.primes = ctx->base->primes.as<uint32_t>() + nsmall;
         la.recip = ctx->base->recip.as<uint64_t>() + nsmall;
         la.n_primes = (uint32_t)(np - nsmall);
         la.out = out;
-        la.strikes = ctx->work_ptr(0);
+        la.strikes = ctx->work_ptr(2);
         const uint64_t chunk = ctx->large_chunk_bits;
         for (uint64_t c0 = 0; c0 < nbits; c0 += chunk) {
             la.bit_lo = c0;
@@ -305,6 +309,7 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
             GB_LAUNCH(gb::launch_large(la, ctx->stream));
         }
         if (popc) GB_LAUNCH(gb::launch_popcount(out, ((nbits + 63) / 64) * 2, popc, ctx->stream));
+        ctx->prof_end();
     }
     return GB_OK;
 }
@@ -558,10 +563,8 @@ int gb_sieve_segment(gb_ctx* ctx, int64_t A_odd, uint64_t n_bits, uint64_t* q_bi
     int rc = ctx->counter.ensure(8);
     if (rc) return rc;
     GB_CUDA(cudaMemsetAsync(ctx->counter.p, 0, 8, ctx->stream));
-    ctx->prof_begin(kProfSieve, n_bits);
     rc = run_sieve(ctx, A_odd, n_bits, reinterpret_cast<uint32_t*>(q_bits),
                    ctx->counter.as<unsigned long long>());
-    ctx->prof_end();
     if (rc) return rc;
     unsigned long long c = 0;
     GB_CUDA(cudaMemcpyAsync(&c, ctx->counter.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -677,9 +680,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
             GB_CUDA(cudaMemsetAsync(pm, 0, n_count * 4, s));
         }
 
-        ctx->prof_begin(kProfSieve, qw * 64);
         if ((rc = run_sieve(ctx, B, qw * 64, ctx->q.as<uint32_t>(), nullptr))) return rc;
-        ctx->prof_end();
 
         gb::CoverArgs ca{};
         ca.Q = ctx->q.as<uint64_t>();
@@ -992,7 +993,9 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
             la.recip = ctx->base->recip.as<uint64_t>() + nsmall;
             la.n_primes = (uint32_t)(np - nsmall);
             la.Q = ctx->bq.as<uint32_t>();
-            la.strikes = ctx->work_ptr(0);
+            la.strikes = ctx->work_ptr(2);
+            ctx->prof_end();
+            ctx->prof_begin(kProfLarge, qwords * 64);
             if (np > nsmall) GB_LAUNCH(gb::launch_large_batch(la, ls));
         }
         ctx->prof_end();
@@ -1162,11 +1165,11 @@ int gb_profile_enable(gb_ctx* ctx, int enable)
     int rc = ctx->prof_collect();
     if (rc) return rc;
     for (int k = 0; k < GB_PROF_KINDS; ++k) { ctx->prof_ms[k] = 0; ctx->prof_launches[k] = 0; ctx->prof_units[k] = 0; }
-    ctx->work_strikes = ctx->work_iters = 0;
+    ctx->work_strikes = ctx->work_iters = ctx->work_large = 0;
     ctx->kernels = 0;
     if (enable && !ctx->work.p) {
-        if ((rc = ctx->work.ensure(16))) return rc;
-        GB_CUDA(cudaMemset(ctx->work.p, 0, 16));
+        if ((rc = ctx->work.ensure(24))) return rc;
+        GB_CUDA(cudaMemset(ctx->work.p, 0, 24));
     }
     ctx->profiling = enable != 0;
     return GB_OK;
@@ -1193,7 +1196,7 @@ int gb_profile_kernels(gb_ctx* ctx, uint64_t* kernels)
     return GB_OK;
 }
 
-int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterations)
+int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterations, uint64_t* large_strikes)
 {
     if (!ctx) return fail(GB_EINVAL, "NULL argument");
     GB_CUDA(cudaSetDevice(ctx->cfg.device));
@@ -1201,6 +1204,7 @@ int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterat
     if (rc) return rc;
     if (sieve_strikes) *sieve_strikes = ctx->work_strikes;
     if (cover_iterations) *cover_iterations = ctx->work_iters;
+    if (large_strikes) *large_strikes = ctx->work_large;
     return GB_OK;
 }
 

@@ -4,8 +4,8 @@
 // arXiv 2603.02621: the segment length and P1 are the knobs of Sec. 2.3 and
 // Sec. 2.4; the others are this implementation's).
 //
-// Coordinate descent: each parameter in turn is set to each of its candidates,
-// the others held at the best so far; a candidate is timed as the best of
+// Coordinate descent: each parameter in turn (the sieve tile jointly with the
+// split) is set to each of its candidates, the others held at the best so far; a candidate is timed as the best of
 // `reps` runs after one warm-up run (which also sizes the arenas).  Outputs do
 // not depend on any of these settings, so the search never changes a result.
 #include <algorithm>
@@ -110,17 +110,20 @@ extern "C" int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, 
         Apply apply;
     };
     std::vector<Param> params;
-    params.push_back({{1u << 16, 1u << 17, 1u << 18, 1u << 19, 1u << 20}, [](gb_config& c, uint32_t v) {
-                          // keep the split at the same multiple of the tile
-                          const double m = (double)c.bucket_split / (double)c.tile_bits;
-                          c.tile_bits = v;
-                          c.bucket_split = (uint32_t)std::max(64.0, m * v);
-                          return true;
-                      }});
-    params.push_back({{1, 2, 4, 8, 16}, [](gb_config& c, uint32_t v) {
-                          c.bucket_split = (uint32_t)std::min<uint64_t>(0xffffffffull, (uint64_t)c.tile_bits * v / 4);
-                          return true;
-                      }});
+    // tile and tile / large-prime split together: value = log2(tile) * 8 +
+    // log2(split / tile) + 2 (split from tile / 4 to 16 tiles)
+    {
+        std::vector<uint32_t> ts;
+        for (uint32_t lt = 16; lt <= 20; ++lt)
+            for (uint32_t m = 0; m <= 6; ++m) ts.push_back(lt * 8 + m);
+        params.push_back({ts, [](gb_config& c, uint32_t v) {
+                              const uint32_t lt = v / 8, m = v % 8;
+                              c.tile_bits = 1u << lt;
+                              const uint64_t split = (1ull << lt) << m >> 2;
+                              c.bucket_split = (uint32_t)std::min<uint64_t>(split, 0xffffffffull);
+                              return true;
+                          }});
+    }
     params.push_back({{1u << 11, 1u << 12, 1u << 13, 1u << 14, 1u << 15}, [](gb_config& c, uint32_t v) {
                           if (c.p2 && v >= c.p2) return false;
                           c.p1 = v;

@@ -88,7 +88,7 @@ SIGNATURES = {
                             POINTER(gb_config), POINTER(ctypes.c_double)]),
     "gb_profile_enable": (c_int, [c_void_p, c_int]),
     "gb_profile_read": (c_int, [c_void_p, POINTER(ctypes.c_double), POINTER(c_uint64), POINTER(c_uint64)]),
-    "gb_profile_work": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64)]),
+    "gb_profile_work": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), POINTER(c_uint64)]),
     "gb_profile_kernels": (c_int, [c_void_p, POINTER(c_uint64)]),
     "gb_bitset_bytes": (c_uint64, [c_uint64]),
     "gb_strerror": (c_char_p, [c_int]),
@@ -241,8 +241,8 @@ def _verify(fn, name, ctx, lo, hi, P, *, hist_cap, pmin, segs, seg_hist_stride, 
     return out
 
 
-GB_PROF_KINDS = 4
-PROF_NAMES = ("sieve", "cover", "retry", "reduce")
+GB_PROF_KINDS = 5
+PROF_NAMES = ("sieve", "cover", "retry", "reduce", "large")
 
 
 def gb_profile_enable(ctx: int, enable: bool = True) -> None:
@@ -258,9 +258,9 @@ def gb_profile_read(ctx: int) -> dict:
 
 
 def gb_profile_work(ctx: int) -> dict:
-    a, b = c_uint64(), c_uint64()
-    _check(load().gb_profile_work(ctx, ctypes.byref(a), ctypes.byref(b)), "gb_profile_work")
-    return dict(sieve_strikes=a.value, cover_iterations=b.value)
+    a, b, c = c_uint64(), c_uint64(), c_uint64()
+    _check(load().gb_profile_work(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "gb_profile_work")
+    return dict(sieve_strikes=a.value, cover_iterations=b.value, large_strikes=c.value)
 
 
 def gb_query(ctx: int, n: int) -> int:
