@@ -12,6 +12,7 @@
 // Sec. 2.3 of GoldbachGPU (arXiv 2603.02621) describes the segment loop and its
 // two phases; the structure above keeps them and moves the sieve to the device.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -149,6 +150,39 @@ struct gb_ctx {
     DevBuf qn, qout;                  // single-n queries: inputs, outputs + invalid-n counter
     HostBuf hstage;
     bool batch_graph = true;          // batch kernels as one CUDA graph (GB_BATCH_GRAPH=0: plain launches)
+    // bucket sieve of the primes >= 2^20 (GB_LARGE=bucket); by default they
+    // are struck by global atomics, measured faster on GB300
+    bool bucket_large = false;
+    uint32_t fill_grid = 0;           // persistent fill CTAs
+    uint32_t bcap = 0;                // entries per (CTA, bucket tile) list
+    uint64_t bucket_overflows = 0;    // chunks redone by the atomic kernel
+    DevBuf blists, bcounts, bflags;
+
+    // size the bucket lists for large primes [nsmall, np) and zero nchunks overflow flags
+    int bucket_setup(uint64_t nsmall, uint64_t np, uint32_t nchunks)
+    {
+        if (!fill_grid) {
+            fill_grid = gb::bucket_fill_grid();
+            if (!fill_grid) return fail(GB_ECUDA, "bucket fill occupancy");
+        }
+        // hits per tile ~ 2^20 * sum 1/p over the large primes (Mertens:
+        // ln ln p_last - ln ln p_first), shared by the fill CTAs; a CTA's
+        // share is at most its first block of 256 primes plus the mean
+        const double p0 = (double)base->h_primes[nsmall], p1 = (double)base->h_primes[np - 1];
+        const double T = (double)(1u << gb::kBucketTileLog2);
+        const double sinv = std::log(std::log(p1)) - std::log(std::log(p0)) + 1.0 / p0;
+        const double mean = T * sinv / fill_grid;
+        const double wmax = 256.0 * (T / p0 + 1.0);
+        double c = mean + wmax + 8.0 * std::sqrt(mean + wmax) + 64.0;
+        bcap = ((uint32_t)c + 31u) & ~31u;
+        int rc;
+        const size_t lists = (size_t)fill_grid * gb::kMaxBuckets * bcap * 4;
+        if ((rc = blists.ensure(lists)) || (rc = bcounts.ensure((size_t)fill_grid * gb::kMaxBuckets * 4)) ||
+            (rc = bflags.ensure((size_t)nchunks * 4)))
+            return rc;
+        GB_CUDA(cudaMemsetAsync(bflags.p, 0, (size_t)nchunks * 4, stream));
+        return GB_OK;
+    }
     bool capturing = false;           // cap_stream is being captured (profiling events become graph nodes)
     cudaStream_t cap_stream = nullptr;  // private stream the batch graph is captured on
     cudaGraphExec_t bgraph = nullptr;
@@ -302,11 +336,64 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
         la.n_primes = (uint32_t)(np - nsmall);
         la.out = out;
         la.strikes = ctx->work_ptr(2);
-        const uint64_t chunk = ctx->large_chunk_bits;
-        for (uint64_t c0 = 0; c0 < nbits; c0 += chunk) {
-            la.bit_lo = c0;
-            la.bit_hi = std::min(nbits, c0 + chunk);
-            GB_LAUNCH(gb::launch_large(la, ctx->stream));
+        // primes of at least a bucket tile (2^20) go to the bucket sieve; those
+        // between the split and a bucket tile hit a tile several times and
+        // keep the atomic kernel
+        const uint64_t nbucket_lo = ctx->bucket_large ? std::max<uint64_t>(nsmall, ctx->pi((1u << gb::kBucketTileLog2) - 1)) : np;
+        if (nbucket_lo < np) {
+            // bucket sieve, chunk by chunk of at most 2^30 bits; a chunk whose
+            // lists overflowed is struck again by the atomic kernel below
+            const uint64_t chunk = (uint64_t)gb::kMaxBuckets << gb::kBucketTileLog2;
+            const uint32_t nchunks = (uint32_t)((nbits + chunk - 1) / chunk);
+            int rc = ctx->bucket_setup(nbucket_lo, np, nchunks);
+            if (rc) return rc;
+            gb::BucketFillArgs fa{};
+            fa.primes = ctx->base->primes.as<uint32_t>() + nbucket_lo;
+            fa.recip = ctx->base->recip.as<uint64_t>() + nbucket_lo;
+            fa.n_primes = (uint32_t)(np - nbucket_lo);
+            fa.lists = ctx->blists.as<uint32_t>();
+            fa.counts = ctx->bcounts.as<uint32_t>();
+            fa.cap = ctx->bcap;
+            fa.strikes = ctx->work_ptr(2);
+            gb::BucketApplyArgs aa{};
+            aa.lists = fa.lists;
+            aa.counts = fa.counts;
+            aa.G = ctx->fill_grid;
+            aa.cap = ctx->bcap;
+            for (uint32_t c = 0; c < nchunks; ++c) {
+                const uint64_t c0 = (uint64_t)c * chunk, span = std::min(nbits - c0, chunk);
+                fa.single = gb::BucketPiece{B, c0, c0 + span, 0};
+                fa.K = aa.K = (uint32_t)((span + (1u << gb::kBucketTileLog2) - 1) >> gb::kBucketTileLog2);
+                fa.overflow = ctx->bflags.as<unsigned int>() + c;
+                aa.q = out + c0 / 32;
+                aa.span = span;
+                GB_LAUNCH(gb::launch_bucket_fill(fa, ctx->fill_grid, ctx->stream));
+                GB_LAUNCH(gb::launch_bucket_apply(aa, ctx->stream));
+            }
+            std::vector<unsigned int> flags(nchunks);
+            GB_CUDA(cudaMemcpyAsync(flags.data(), ctx->bflags.p, nchunks * 4, cudaMemcpyDeviceToHost, ctx->stream));
+            GB_CUDA(cudaStreamSynchronize(ctx->stream));
+            for (uint32_t c = 0; c < nchunks; ++c) {
+                if (!flags[c]) continue;
+                gb::LargeArgs lb = la;
+                lb.primes = fa.primes;
+                lb.recip = fa.recip;
+                lb.n_primes = fa.n_primes;
+                lb.bit_lo = (uint64_t)c * chunk;
+                lb.bit_hi = std::min(nbits, lb.bit_lo + chunk);
+                lb.strikes = nullptr;
+                ctx->bucket_overflows += 1;
+                GB_LAUNCH(gb::launch_large(lb, ctx->stream));
+            }
+        }
+        if (nbucket_lo > nsmall) {
+            la.n_primes = (uint32_t)(nbucket_lo - nsmall);
+            const uint64_t chunk = ctx->large_chunk_bits;
+            for (uint64_t c0 = 0; c0 < nbits; c0 += chunk) {
+                la.bit_lo = c0;
+                la.bit_hi = std::min(nbits, c0 + chunk);
+                GB_LAUNCH(gb::launch_large(la, ctx->stream));
+            }
         }
         if (popc) GB_LAUNCH(gb::launch_popcount(out, ((nbits + 63) / 64) * 2, popc, ctx->stream));
         ctx->prof_end();
@@ -473,6 +560,7 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     if (const char* e = getenv("GB_WARP_SPLIT")) ctx->warp_split = atoi(e);
     if (const char* e = getenv("GB_COVER")) ctx->generic_cover = std::string(e) == "generic";
     if (const char* e = getenv("GB_BATCH_GRAPH")) ctx->batch_graph = atoi(e) != 0;
+    if (const char* e = getenv("GB_LARGE")) ctx->bucket_large = std::string(e) == "bucket";
     if (const char* e = getenv("GB_LARGE_CHUNK_LOG2")) {
         const int v = atoi(e);
         if (v >= 16 && v <= 40) ctx->large_chunk_bits = 1ull << v;
@@ -507,6 +595,7 @@ int gb_init_shared(gb_ctx** out, const gb_ctx* parent, void* stream)
     ctx->generic_cover = parent->generic_cover;
     ctx->batch_graph = parent->batch_graph;
     ctx->large_chunk_bits = parent->large_chunk_bits;
+    ctx->bucket_large = parent->bucket_large;
     *out = ctx;
     return GB_OK;
 }
@@ -523,7 +612,7 @@ void gb_destroy(gb_ctx* ctx)
                       &ctx->maxkey, &ctx->maxkey2, &ctx->unres, &ctx->retry, &ctx->retry_count, &ctx->summary,
                       &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work,
                       &ctx->bq, &ctx->bhist, &ctx->bkeys, &ctx->bunres, &ctx->bdesc, &ctx->brecords, &ctx->brows,
-                      &ctx->qn, &ctx->qout};
+                      &ctx->qn, &ctx->qout, &ctx->blists, &ctx->bcounts, &ctx->bflags};
     for (DevBuf* b : bufs) b->release();
     delete ctx;
 }

@@ -283,6 +283,43 @@ struct ReduceBatchArgs {
 };
 cudaError_t launch_reduce_batch(const ReduceBatchArgs& a, uint32_t grid, cudaStream_t s);
 
+// Bucket sieve for the primes above the tile split (gb_bucket.cu): a chunk
+// of at most kMaxBuckets bucket tiles of 2^kBucketTileLog2 bits; pieces are
+// runs of window bits with their own number base (one piece for a plain
+// window, one per range of a batch group)
+constexpr uint32_t kBucketTileLog2 = 20;
+constexpr uint32_t kMaxBuckets = 1024;
+struct BucketPiece {
+    int64_t B;                  // odd number of the window's bit 0
+    uint64_t r_lo, r_hi;        // window bits [r_lo, r_hi) in this chunk
+    uint64_t pos;               // chunk bit of window bit r_lo
+};
+struct BucketFillArgs {
+    const BucketPiece* pieces;  // device array, or nullptr: the one piece `single`
+    uint32_t n_pieces;
+    BucketPiece single;
+    uint32_t K;                 // bucket tiles in the chunk (<= kMaxBuckets)
+    const uint32_t* primes;     // the large primes
+    const uint64_t* recip;
+    uint32_t n_primes;
+    uint32_t* lists;            // [grid][K][cap] 20-bit offsets
+    uint32_t* counts;           // [grid][K]
+    uint32_t cap;
+    unsigned int* overflow;     // set if a list overflowed (entries dropped)
+    unsigned long long* strikes;
+};
+struct BucketApplyArgs {
+    const uint32_t* lists;
+    const uint32_t* counts;
+    uint32_t G, K, cap;
+    uint32_t* q;                // 32-bit word of the chunk's bit 0
+    uint64_t span;              // chunk bits
+};
+uint32_t bucket_fill_grid();    // persistent fill CTAs on this device (0 on error)
+size_t bucket_fill_smem(uint32_t K);
+cudaError_t launch_bucket_fill(const BucketFillArgs& a, uint32_t grid, cudaStream_t s);
+cudaError_t launch_bucket_apply(const BucketApplyArgs& a, cudaStream_t s);
+
 // Single-n queries (gb_query.cu): one CTA per n, p_min over primes[1..K]
 struct QueryArgs {
     const uint64_t* n;          // device: even n, 4 <= n < 2^63
