@@ -254,6 +254,16 @@ int gb_server_stats(gb_server* srv, uint64_t* submitted, uint64_t* completed, ui
 /* finishes every queued request, then stops the lanes */
 void gb_server_destroy(gb_server* srv);
 
+/* Goldbach partition counts (Sec. 4.5, future work there): counts[j] = r(n)
+ * for n = lo + 2j in [lo, hi), r(n) = the number of prime pairs p <= q with
+ * p + q = n (r(4) = 1, r(100) = 6).  Computed on the GPU from the odd-only
+ * prime bitset of [1, hi) and its bit-reversed copy: for each n, popcount of
+ * the AND of the bitset with the reversed one shifted to n, over p <= n/2
+ * (about n/128 word steps per n).  lo even >= 4, hi even, hi <= 2^34 and
+ * hi <= base_limit^2, at most 2^28 n per call; counts host or device.
+ * Synchronous. */
+int gb_partitions(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t* counts);
+
 /* gb_verify_range without memory allocation (the paper has no counterpart:
  * this is a calling convention of this library).  Some callers must not call
  * cudaMalloc while they run -- it can synchronize the device and stall every

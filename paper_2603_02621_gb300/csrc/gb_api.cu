@@ -148,6 +148,7 @@ struct gb_ctx {
     // batched mode
     DevBuf bq, bhist, bkeys, bunres, bdesc, brecords, brows;
     DevBuf qn, qout;                  // single-n queries: inputs, outputs + invalid-n counter
+    DevBuf part_p, part_rev, part_out;  // partition counts: prime bits, reversed bits, counts
     HostBuf hstage;
     bool batch_graph = true;          // batch kernels as one CUDA graph (GB_BATCH_GRAPH=0: plain launches)
     // bucket sieve of the primes >= 2^20 (GB_LARGE=bucket); by default they
@@ -612,7 +613,8 @@ void gb_destroy(gb_ctx* ctx)
                       &ctx->maxkey, &ctx->maxkey2, &ctx->unres, &ctx->retry, &ctx->retry_count, &ctx->summary,
                       &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work,
                       &ctx->bq, &ctx->bhist, &ctx->bkeys, &ctx->bunres, &ctx->bdesc, &ctx->brecords, &ctx->brows,
-                      &ctx->qn, &ctx->qout, &ctx->blists, &ctx->bcounts, &ctx->bflags};
+                      &ctx->qn, &ctx->qout, &ctx->blists, &ctx->bcounts, &ctx->bflags,
+                      &ctx->part_p, &ctx->part_rev, &ctx->part_out};
     for (DevBuf* b : bufs) b->release();
     delete ctx;
 }
@@ -1238,6 +1240,45 @@ int gb_query_batch(gb_ctx* ctx, const uint64_t* n, uint32_t count, uint32_t P, u
     if (!out_dev) GB_CUDA(cudaMemcpyAsync(p_min, qa.out, (size_t)count * 4, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     if (h_bad) return fail(GB_EINVAL, "n must be even, 4 <= n < 2^63 (device input)");
+    return GB_OK;
+}
+
+int gb_partitions(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t* counts)
+{
+    if (!ctx || (hi > lo && !counts)) return fail(GB_EINVAL, "NULL argument");
+    if ((lo & 1) || (hi & 1) || lo < 4 || hi < lo) return fail(GB_EINVAL, "range must be even, lo >= 4, hi >= lo");
+    if (hi > (1ull << 34)) return fail(GB_EINVAL, "partition counts need hi <= 2^34");
+    const uint64_t count = (hi - lo) / 2;
+    if (count == 0) return GB_OK;
+    if (count > (1ull << 28)) return fail(GB_EINVAL, "at most 2^28 even n per call");
+    GB_CUDA(cudaSetDevice(ctx->cfg.device));
+    cudaStream_t s = ctx->stream;
+    // P covers the odd numbers 1 .. the largest m = (hi - 4) / 2 index
+    const uint64_t mmax = (hi - 4) / 2;
+    const uint64_t words = ((mmax + 1 + 63) / 64) * 2;                  // whole 64-bit words
+    const bool out_dev = is_device_ptr(counts);
+    int rc;
+    if ((rc = ctx->part_p.ensure(words * 4)) || (rc = ctx->part_rev.ensure((words + 1) * 4)) ||
+        (!out_dev && (rc = ctx->part_out.ensure(count * 4))))
+        return rc;
+    if ((rc = run_sieve(ctx, 1, words * 32, ctx->part_p.as<uint32_t>(), nullptr))) return rc;
+    GB_LAUNCH(gb::launch_reverse_bits(ctx->part_p.as<uint32_t>(), ctx->part_rev.as<uint32_t>(), words, s));
+    uint32_t* d_out = out_dev ? counts : ctx->part_out.as<uint32_t>();
+    GB_CUDA(cudaMemsetAsync(d_out, 0, count * 4, s));
+    gb::PartitionArgs pa{};
+    pa.P = ctx->part_p.as<uint32_t>();
+    pa.rev = ctx->part_rev.as<uint32_t>();
+    pa.words = words;
+    pa.lo = lo;
+    pa.count = count;
+    pa.n_blocks = (count + 31) / 32;
+    pa.run_words = 4096;
+    pa.counts = d_out;
+    const uint64_t need = ((hi - 4) / 2) / 2 / 32 + 1;                  // words of the largest n
+    pa.runs = (need + pa.run_words - 1) / pa.run_words;
+    GB_LAUNCH(gb::launch_partitions(pa, s));
+    if (!out_dev) GB_CUDA(cudaMemcpyAsync(counts, d_out, count * 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
     return GB_OK;
 }
 

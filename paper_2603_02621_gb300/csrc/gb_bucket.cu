@@ -214,7 +214,7 @@ size_t bucket_fill_smem(uint32_t K) { return ((size_t)K * (kStage + 2) + kFlushL
 cudaError_t launch_bucket_fill(const BucketFillArgs& a, uint32_t grid, cudaStream_t s)
 {
     if (a.n_primes == 0 || a.K == 0) return cudaSuccess;
-    if (a.K > kMaxBuckets) return cudaErrorInvalidValue;
+    if (a.K > kMaxBuckets || !a.primes || !a.recip || !a.lists || !a.counts || !a.overflow) return cudaErrorInvalidValue;
     const size_t smem = bucket_fill_smem(kMaxBuckets);
     cudaError_t e = cudaFuncSetAttribute(k_bucket_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -225,6 +225,7 @@ cudaError_t launch_bucket_fill(const BucketFillArgs& a, uint32_t grid, cudaStrea
 cudaError_t launch_bucket_apply(const BucketApplyArgs& a, cudaStream_t s)
 {
     if (a.K == 0 || a.span == 0) return cudaSuccess;
+    if (!a.lists || !a.counts || !a.q) return cudaErrorInvalidValue;
     const size_t smem = (size_t)(1u << kBucketTileLog2) / 8;
     cudaError_t e = cudaFuncSetAttribute(k_bucket_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -320,6 +320,21 @@ size_t bucket_fill_smem(uint32_t K);
 cudaError_t launch_bucket_fill(const BucketFillArgs& a, uint32_t grid, cudaStream_t s);
 cudaError_t launch_bucket_apply(const BucketApplyArgs& a, cudaStream_t s);
 
+// Goldbach partition counts (gb_partitions.cu)
+struct PartitionArgs {
+    const uint32_t* P;          // odd-only prime bits of [1, 64 * words / 2 ...): bit i <-> 2i + 1
+    const uint32_t* rev;        // bit-reversed P, words + 1 entries (last one zero)
+    uint64_t words;             // 32-bit words of P
+    uint64_t lo;                // first even n
+    uint64_t count;             // even n in the range
+    uint64_t n_blocks;          // ceil(count / 32)
+    uint64_t runs;              // word runs per n-block
+    uint64_t run_words;         // words per run
+    uint32_t* counts;           // [count], zeroed; r(n) added
+};
+cudaError_t launch_reverse_bits(const uint32_t* P, uint32_t* rev, uint64_t words, cudaStream_t s);
+cudaError_t launch_partitions(const PartitionArgs& a, cudaStream_t s);
+
 // Single-n queries (gb_query.cu): one CTA per n, p_min over primes[1..K]
 struct QueryArgs {
     const uint64_t* n;          // device: even n, 4 <= n < 2^63

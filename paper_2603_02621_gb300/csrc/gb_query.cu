@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(const QueryArgs a)
 cudaError_t launch_query(const QueryArgs& a, cudaStream_t s)
 {
     if (a.count == 0) return cudaSuccess;
+    if (!a.n || !a.primes || !a.recip || !a.out || !a.bad) return cudaErrorInvalidValue;
     const uint32_t grid = a.count < 152u * 16 ? a.count : 152u * 16;
     k_query<<<grid, kQueryThreads, 0, s>>>(a);
     return cudaGetLastError();

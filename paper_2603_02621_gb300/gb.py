@@ -75,6 +75,7 @@ SIGNATURES = {
     "gb_verify_batch": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), c_uint32, c_uint32,
                                 c_void_p, c_void_p, c_uint32]),
     "gb_query": (c_int, [c_void_p, c_uint64, POINTER(c_uint32)]),
+    "gb_partitions": (c_int, [c_void_p, c_uint64, c_uint64, c_void_p]),
     "gb_query_batch": (c_int, [c_void_p, c_void_p, c_uint32, c_uint32, c_void_p]),
     "gb_set_config": (c_int, [c_void_p, POINTER(gb_config)]),
     "gb_init_shared": (c_int, [POINTER(c_void_p), c_void_p, c_void_p]),
@@ -263,6 +264,20 @@ def gb_profile_work(ctx: int) -> dict:
     return dict(sieve_strikes=a.value, cover_iterations=b.value, large_strikes=c.value)
 
 
+def gb_partitions(ctx: int, lo: int, hi: int, out=None):
+    """r(n) for even n in [lo, hi): numpy uint32 array, or filled into `out`
+    (a CUDA int32 tensor of (hi - lo) / 2 entries)."""
+    count = (hi - lo) // 2
+    res = None
+    if out is None:
+        res = np.zeros(max(count, 0), dtype=np.uint32)
+        ptr = int(res.ctypes.data)
+    else:
+        ptr = out.data_ptr()
+    _check(load().gb_partitions(ctx, lo, hi, ptr), "gb_partitions")
+    return res
+
+
 def gb_query(ctx: int, n: int) -> int:
     """p_min(n) (0 if no p <= the context's bound), computed on the GPU."""
     out = c_uint32()
@@ -416,6 +431,9 @@ class Context:
 
     def verify_batch(self, ranges, P=0, **kw):
         return gb_verify_batch(self.handle, ranges, P, **kw)
+
+    def partitions(self, lo, hi, out=None):
+        return gb_partitions(self.handle, lo, hi, out)
 
     def query(self, n):
         return gb_query(self.handle, n)
