@@ -108,16 +108,21 @@ __device__ __forceinline__ void sieve_tile(const SieveArgs& a, uint64_t t0, cons
             pending &= pending - 1;
             const uint32_t q = __shfl_sync(0xffffffffu, p, src);
             const uint32_t j0 = __shfl_sync(0xffffffffu, i0, src);
-            const uint32_t step = 32u * q;
-            uint32_t i = j0 + (uint32_t)lane * q;
-            // step <= 2^15 and i < 2^20: no wrap below
-            for (; i + 3 * step < nb; i += 4 * step) {
-                strike(sm, i);
-                strike(sm, i + step);
-                strike(sm, i + 2 * step);
-                strike(sm, i + 3 * step);
+            // lane l strikes j0 + l q + 32 q k: the step is q whole words, so
+            // the bit in the word, hence the mask, is fixed per lane
+            const uint32_t i = j0 + (uint32_t)lane * q;           // < 2^20 + 2^15: no wrap
+            if (i < nb) {
+                const uint32_t mask = __funnelshift_l(0xfffffffeu, 0xfffffffeu, i);
+                uint32_t* w = sm + (i >> 5);
+                uint32_t* const end = sm + ((nb - (i & 31u) + 31u) >> 5);   // words whose bit i&31 is < nb
+                for (; w + 3 * q < end; w += 4 * q) {
+                    atomicAnd(w, mask);
+                    atomicAnd(w + q, mask);
+                    atomicAnd(w + 2 * q, mask);
+                    atomicAnd(w + 3 * q, mask);
+                }
+                for (; w < end; w += q) atomicAnd(w, mask);
             }
-            for (; i < nb; i += step) strike(sm, i);
         }
     }
     // 2b. larger primes, one thread each
