@@ -154,6 +154,7 @@ struct gb_ctx {
     // bucket sieve of the primes >= 2^20 (GB_LARGE=bucket); by default they
     // are struck by global atomics, measured faster on GB300
     bool bucket_large = false;
+    bool fused = false;               // sieve and block cover fused per CTA (GB_FUSED=1)
     uint32_t fill_grid = 0;           // persistent fill CTAs
     uint32_t bcap = 0;                // entries per (CTA, bucket tile) list
     uint64_t bucket_overflows = 0;    // chunks redone by the atomic kernel
@@ -297,20 +298,17 @@ int fill_defaults(gb_config& c)
 }
 
 // sieve the odd numbers B + 2i, i < nbits, into out (device words) or count only
-int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned long long* popc)
+// tile-sieve arguments for the window (B, nbits): the primes below the split
+// (from 47 on; 3..43 are stamped); *np and *nsmall receive the count of
+// primes <= sqrt(last number) and of those below the split
+int tile_sieve_args(gb_ctx* ctx, int64_t B, uint64_t nbits, gb::SieveArgs& a, uint64_t& np, uint64_t& nsmall)
 {
-    if (nbits == 0) return GB_OK;
     const int64_t last = B + 2 * (int64_t)(nbits - 1);
     const uint64_t r = last > 0 ? isqrt_u64((uint64_t)last) : 0;
     if (r > ctx->L) return fail(GB_EINVAL, "window beyond base_limit^2");
-    const uint64_t np = ctx->pi(r);                 // primes <= sqrt(last)
-    // primes from bucket_split on are struck by the large-prime kernel, chunk
-    // by chunk, into the output words (the tile kernel only counts bits when
-    // there are none)
-    const uint64_t nsmall = std::min<uint64_t>(np, std::max<uint64_t>(ctx->pi(ctx->cfg.bucket_split - 1), gb::kFirstStrikeIdx));
-    const bool large = np > nsmall && out;
-    if (np > nsmall && !out) return fail(GB_EINVAL, "internal: large primes need an output buffer");
-    gb::SieveArgs a{};
+    np = ctx->pi(r);                                // primes <= sqrt(last)
+    nsmall = std::min<uint64_t>(np, std::max<uint64_t>(ctx->pi(ctx->cfg.bucket_split - 1), gb::kFirstStrikeIdx));
+    a = gb::SieveArgs{};
     a.B = B;
     a.nbits = nbits;
     a.tile_bits = ctx->cfg.tile_bits;
@@ -322,9 +320,24 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
     a.n_warp = (uint32_t)nwarp;
     a.n_primes = (uint32_t)nstrike;
     a.wheel = ctx->base->wheel.as<uint32_t>();
+    a.strikes = ctx->work_ptr(0);
+    return GB_OK;
+}
+
+int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned long long* popc)
+{
+    if (nbits == 0) return GB_OK;
+    // primes from bucket_split on are struck by the large-prime kernel, chunk
+    // by chunk, into the output words (the tile kernel only counts bits when
+    // there are none)
+    gb::SieveArgs a{};
+    uint64_t np = 0, nsmall = 0;
+    int rc0 = tile_sieve_args(ctx, B, nbits, a, np, nsmall);
+    if (rc0) return rc0;
+    const bool large = np > nsmall && out;
+    if (np > nsmall && !out) return fail(GB_EINVAL, "internal: large primes need an output buffer");
     a.out = out;
     a.popcount = large ? nullptr : popc;
-    a.strikes = ctx->work_ptr(0);
     ctx->prof_begin(kProfSieve, nbits);
     GB_LAUNCH(gb::launch_sieve(a, (int)ctx->cfg.cta_threads, ctx->stream));
     ctx->prof_end();
@@ -562,6 +575,7 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     if (const char* e = getenv("GB_COVER")) ctx->generic_cover = std::string(e) == "generic";
     if (const char* e = getenv("GB_BATCH_GRAPH")) ctx->batch_graph = atoi(e) != 0;
     if (const char* e = getenv("GB_LARGE")) ctx->bucket_large = std::string(e) == "bucket";
+    if (const char* e = getenv("GB_FUSED")) ctx->fused = atoi(e) != 0;
     if (const char* e = getenv("GB_LARGE_CHUNK_LOG2")) {
         const int v = atoi(e);
         if (v >= 16 && v <= 40) ctx->large_chunk_bits = 1ull << v;
@@ -597,6 +611,7 @@ int gb_init_shared(gb_ctx** out, const gb_ctx* parent, void* stream)
     ctx->batch_graph = parent->batch_graph;
     ctx->large_chunk_bits = parent->large_chunk_bits;
     ctx->bucket_large = parent->bucket_large;
+    ctx->fused = parent->fused;
     *out = ctx;
     return GB_OK;
 }
@@ -771,8 +786,6 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
             GB_CUDA(cudaMemsetAsync(pm, 0, n_count * 4, s));
         }
 
-        if ((rc = run_sieve(ctx, B, qw * 64, ctx->q.as<uint32_t>(), nullptr))) return rc;
-
         gb::CoverArgs ca{};
         ca.Q = ctx->q.as<uint64_t>();
         ca.H = H;
@@ -804,12 +817,41 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
             ca.cta_words = std::min<uint32_t>(3840, (uint32_t)(S / 64));
             ca.chunks_per_seg = (uint32_t)((S / 64 + ca.cta_words - 1) / ca.cta_words);
         }
+        // fused sieve + cover (GB_FUSED=1): block cover, no large primes, the
+        // chunk plus its partner halo within one shared-memory tile
+        bool fused = false;
+        gb::SieveArgs fsv{};
+        const uint32_t P1max = ctx->base->h_primes[K1];           // largest prime of the first pass
+        if (ctx->fused && KA &&
+            (2ull * ca.cta_words + (H - 4) / 64 + 3 - gb::seg_cover_offset(H, P1max)) * 32 <= gb::kFusedTileBits) {
+            uint64_t np = 0, nsmall = 0;
+            if ((rc = tile_sieve_args(ctx, B, qw * 64, fsv, np, nsmall))) return rc;
+            fused = np <= nsmall;
+            fsv.tile_bits = gb::kFusedTileBits;
+        }
+        bool q_in_hbm = false;
+        if (!fused) {
+            if ((rc = run_sieve(ctx, B, qw * 64, ctx->q.as<uint32_t>(), nullptr))) return rc;
+            q_in_hbm = true;
+        }
         ctx->prof_begin(kProfCover, n_count);
-        if (KA) GB_LAUNCH(gb::launch_cover_fast(ca, KA, s));
+        if (fused) GB_LAUNCH(gb::launch_seg_cover(ca, fsv, KA, P1max, s));
+        else if (KA) GB_LAUNCH(gb::launch_cover_fast(ca, KA, s));
         else GB_LAUNCH(gb::launch_cover(ca, (int)cfg.cta_threads, s));
         ctx->prof_end();
 
-        if (retry) {
+        if (retry && fused) {
+            // the retry pass reads Q from global memory: sieve the slab there
+            // only if some word was left open
+            unsigned int cnt = 0;
+            GB_CUDA(cudaMemcpyAsync(&cnt, ctx->retry_count.p, 4, cudaMemcpyDeviceToHost, s));
+            GB_CUDA(cudaStreamSynchronize(s));
+            if (cnt) {
+                if ((rc = run_sieve(ctx, B, qw * 64, ctx->q.as<uint32_t>(), nullptr))) return rc;
+                q_in_hbm = true;
+            }
+        }
+        if (retry && q_in_hbm) {
             gb::RetryArgs ra{};
             ra.Q = ca.Q;
             ra.H = H;

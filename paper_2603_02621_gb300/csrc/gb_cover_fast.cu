@@ -32,6 +32,7 @@
 #include <utility>
 
 #include "gb_internal.cuh"
+#include "gb_sieve_tile.cuh"
 
 namespace gb {
 
@@ -209,9 +210,18 @@ __device__ __forceinline__ void run_block_tracked(std::integer_sequence<int, J..
     (block_step_tracked<K0 + J, K0, NR, KH>(R, C, cum, last, lastbits), ...);
 }
 
+// a word of the q window: read-only global load, or a shared-memory load when
+// the window is a tile the same CTA has just sieved (fused kernel)
+template <bool SQ>
+__device__ __forceinline__ uint32_t ldq(const uint32_t* p)
+{
+    if constexpr (SQ) return *p;
+    else return __ldg(p);
+}
+
 // block K0 on one word with tracking only (no histogram): the key of its
 // largest p_min with the smallest n, 0 if the block set no bit
-template <int K0>
+template <int K0, bool SQ>
 __device__ __forceinline__ unsigned long long track_word(const uint32_t* Qc, uint32_t D0w, uint32_t wrel, uint32_t C,
                                                          uint32_t j_cta)
 {
@@ -219,7 +229,7 @@ __device__ __forceinline__ unsigned long long track_word(const uint32_t* Qc, uin
     constexpr int C0 = block_c0(K0);
     uint32_t R[NR];
 #pragma unroll
-    for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - C0 - t);
+    for (int t = 0; t < NR; ++t) R[t] = ldq<SQ>(Qc + wrel + D0w - C0 - t);
     uint32_t last = 0, lastbits = 0;
     track_block_steps<K0, NR>(std::make_integer_sequence<int, kBlock>{}, R, C, last, lastbits);
     if (!last) return 0;
@@ -230,7 +240,7 @@ __device__ __forceinline__ unsigned long long track_word(const uint32_t* Qc, uin
 // Later block K0 over a warp's list, batches of 32 words (one per lane),
 // with per-word tracking of the last step that set a bit; words still open
 // are compacted in place at the front of the list (writes never pass reads).
-template <int K0>
+template <int K0, bool SQ>
 __device__ __forceinline__ uint32_t later_block_warp(const uint32_t* Qc, uint32_t D0w, uint16_t* lw, uint32_t* lc,
                                                      uint32_t n_in, uint32_t* shist, uint32_t j_cta,
                                                      unsigned long long& best, uint32_t& nsteps)
@@ -252,7 +262,7 @@ __device__ __forceinline__ uint32_t later_block_warp(const uint32_t* Qc, uint32_
             wrel = lw[e];
             C = lc[e];
 #pragma unroll
-            for (int t = 0; t < NR; ++t) R[t] = __ldg(Qc + wrel + D0w - C0 - t);
+            for (int t = 0; t < NR; ++t) R[t] = ldq<SQ>(Qc + wrel + D0w - C0 - t);
         } else {
 #pragma unroll
             for (int t = 0; t < NR; ++t) R[t] = 0;
@@ -283,6 +293,7 @@ __device__ __forceinline__ uint32_t later_block_warp(const uint32_t* Qc, uint32_
 
 // Probing over a warp's list: the warp takes the open n one at a time, lane t
 // probing the prime k + t; the lowest set bit of the ballot is p_min.
+template <bool SQ>
 __device__ __forceinline__ void probe_warp(const CoverArgs& a, const uint32_t* Qc, const uint16_t* lw,
                                            const uint32_t* lc, uint32_t n_in, uint32_t k_first, uint64_t w_begin,
                                            uint32_t j_cta, uint32_t seg, unsigned long long& best, uint32_t& nsteps)
@@ -301,7 +312,7 @@ __device__ __forceinline__ void probe_warp(const CoverArgs& a, const uint32_t* Q
                 uint32_t bit = 0;
                 if (kt < a.K) {
                     const uint32_t i = rel + ((a.H - __ldg(a.primes + 1 + kt) - 1) >> 1);
-                    bit = (__ldg(Qc + (i >> 5)) >> (i & 31)) & 1u;
+                    bit = (ldq<SQ>(Qc + (i >> 5)) >> (i & 31)) & 1u;
                 }
                 const unsigned hb = __ballot_sync(0xffffffffu, bit);
                 if (lane == 0) nsteps += 32;
@@ -344,9 +355,9 @@ __device__ __forceinline__ void probe_warp(const CoverArgs& a, const uint32_t* Q
 // a.Q, 32 even n each), all in segment (row) seg, whose first n has
 // segment-relative index j_cta.  Called by every thread of the CTA; smem holds
 // the per-warp lists; shist / smax are the CTA's shared counters.
-template <int NT, int NB>
-__device__ __forceinline__ void cover_chunk(const CoverArgs& a, uint32_t seg, uint64_t w_begin, uint64_t w_end,
-                                            uint32_t j_cta, uint32_t* smem, uint32_t* shist,
+template <int NT, int NB, bool SQ>
+__device__ __forceinline__ void cover_chunk(const CoverArgs& a, const uint32_t* Qc, uint32_t seg, uint64_t w_begin,
+                                            uint64_t w_end, uint32_t j_cta, uint32_t* smem, uint32_t* shist,
                                             unsigned long long& smax)
 {
     constexpr int NW = NT / 32;
@@ -361,7 +372,6 @@ __device__ __forceinline__ void cover_chunk(const CoverArgs& a, uint32_t seg, ui
     if (threadIdx.x == 0) smax = 0;
     __syncthreads();
 
-    const uint32_t* Qc = reinterpret_cast<const uint32_t*>(a.Q) + w_begin;   // CTA-relative words
     const uint32_t D0w = ((a.H - 4) >> 1) >> 5;            // word offset of the p = 3 partner
     const uint32_t nw_cta = (uint32_t)(w_end > w_begin ? w_end - w_begin : 0);
     const uint64_t n_left = a.n_count - 32 * w_begin;       // n from the CTA's first n to the window end
@@ -401,7 +411,7 @@ __device__ __forceinline__ void cover_chunk(const CoverArgs& a, uint32_t seg, ui
                 // the top word read, wl + 2, lies at most one word past the CTA's
                 // last word: inside the q window, which runs past the slab
 #pragma unroll
-                for (int t = 0; t < NR3; ++t) R[t] = __ldg(Qc + wl + 2 + D0w - t);
+                for (int t = 0; t < NR3; ++t) R[t] = ldq<SQ>(Qc + wl + 2 + D0w - t);
             } else {
 #pragma unroll
                 for (int t = 0; t < NR3; ++t) R[t] = 0;
@@ -425,10 +435,10 @@ __device__ __forceinline__ void cover_chunk(const CoverArgs& a, uint32_t seg, ui
     }
     __syncwarp();
     unsigned long long best = 0;
-    if constexpr (NB >= 2) n_open = later_block_warp<64>(Qc, D0w, lw, lc, n_open, shist, j_cta, best, nsteps);
-    if constexpr (NB >= 3) n_open = later_block_warp<128>(Qc, D0w, lw, lc, n_open, shist, j_cta, best, nsteps);
-    if constexpr (NB >= 4) n_open = later_block_warp<192>(Qc, D0w, lw, lc, n_open, shist, j_cta, best, nsteps);
-    probe_warp(a, Qc, lw, lc, n_open, (uint32_t)(kBlock * NB), w_begin, j_cta, seg, best, nsteps);
+    if constexpr (NB >= 2) n_open = later_block_warp<64, SQ>(Qc, D0w, lw, lc, n_open, shist, j_cta, best, nsteps);
+    if constexpr (NB >= 3) n_open = later_block_warp<128, SQ>(Qc, D0w, lw, lc, n_open, shist, j_cta, best, nsteps);
+    if constexpr (NB >= 4) n_open = later_block_warp<192, SQ>(Qc, D0w, lw, lc, n_open, shist, j_cta, best, nsteps);
+    probe_warp<SQ>(a, Qc, lw, lc, n_open, (uint32_t)(kBlock * NB), w_begin, j_cta, seg, best, nsteps);
 
     // maximum: warp, CTA
     {
@@ -448,7 +458,7 @@ __device__ __forceinline__ void cover_chunk(const CoverArgs& a, uint32_t seg, ui
             const uint32_t j0 = 32 * w;
             if (n_rel_end - j0 < 32) C = 0xffffffffu << (n_rel_end - j0);
             if (a.has_n4 && w_begin + w == 0) C |= 1u;
-            const unsigned long long key = track_word<0>(Qc, D0w, (uint32_t)w, C, j_cta);
+            const unsigned long long key = track_word<0, SQ>(Qc, D0w, (uint32_t)w, C, j_cta);
             if (key > best) best = key;
         }
         if (a.has_n4 && w_begin == 0 && threadIdx.x == 0) {
@@ -492,7 +502,81 @@ __global__ void __launch_bounds__(NT, 4) k_cover_fast(const CoverArgs a)
     const uint64_t n_words32 = (a.n_count + 31) / 32;
     if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
     if (w_end > n_words32) w_end = n_words32;
-    cover_chunk<NT, NB>(a, seg, w_begin, w_end, (uint32_t)(32 * (w_begin - seg_w0)), smem, shist, smax);
+    cover_chunk<NT, NB, false>(a, reinterpret_cast<const uint32_t*>(a.Q) + w_begin, seg, w_begin, w_end,
+                               (uint32_t)(32 * (w_begin - seg_w0)), smem, shist, smax);
+}
+
+// Sieve and cover fused per CTA: the CTA sieves the q bits its chunk of
+// coverage words reads into shared memory with the tile sieve and runs the
+// block cover on them there; Q never goes through global memory.  The cover
+// reads window words from w_begin + off_w (the partner offset of the largest
+// prime of the pass, (H - P1 - 1) / 2 bits) to w_end + (H - 4) / 64 + 2, so
+// the tile starts at word w_begin + off_w.
+template <int NT, int NB>
+__global__ void __launch_bounds__(NT, 2) k_seg_cover(const CoverArgs a, const SieveArgs sv, uint32_t off_w)
+{
+    extern __shared__ uint32_t smem[];                      // [lists | stamp tables | tile]
+    __shared__ uint32_t shist[kBlock * NB + 1];
+    __shared__ unsigned long long smax;
+    constexpr int NW = NT / 32;
+    const uint32_t cap = (2 * a.cta_words + 96 * NW - 1) / (96 * NW) * 96;
+    uint32_t* lists = smem;
+    uint32_t* wt = smem + (NW * cap * 6) / 4;
+    uint32_t* tile = wt + ((kWheelWords + 3 + 3) & ~3u);    // 16-byte aligned
+    const uint64_t wps = 2ull * a.words_per_seg;
+    const uint32_t seg = blockIdx.x / a.chunks_per_seg;
+    const uint32_t chunk = blockIdx.x % a.chunks_per_seg;
+    const uint64_t seg_w0 = (uint64_t)seg * wps;
+    const uint64_t w_begin = seg_w0 + (uint64_t)chunk * (2ull * a.cta_words);
+    uint64_t w_end = w_begin + 2ull * a.cta_words;
+    const uint64_t n_words32 = (a.n_count + 31) / 32;
+    if (w_end > seg_w0 + wps) w_end = seg_w0 + wps;
+    if (w_end > n_words32) w_end = n_words32;
+    for (uint32_t i = threadIdx.x; i < kWheelWords; i += NT) wt[i] = sv.wheel[i];
+    // tile word k is window word w_begin + off_w + k; the cover's Qc[k] is
+    // window word w_begin + k and is only read at k >= off_w
+    sieve_tile<NT>(sv, 32ull * (w_begin + off_w), wt, tile);
+    cover_chunk<NT, NB, true>(a, tile - off_w, seg, w_begin, w_end, (uint32_t)(32 * (w_begin - seg_w0)), lists, shist,
+                              smax);
+}
+
+template <int NB>
+static cudaError_t launch_seg_nb(const CoverArgs& a, const SieveArgs& sv, uint32_t off_w, cudaStream_t s)
+{
+    constexpr int NT = 256;
+    const unsigned grid = a.nseg * a.chunks_per_seg;
+    if (grid == 0) return cudaSuccess;
+    const uint32_t cap = (2 * a.cta_words + 96 * (NT / 32) - 1) / (96 * (NT / 32)) * 96;
+    const size_t smem = (size_t)(NT / 32) * cap * 6 + ((kWheelWords + 3 + 3) & ~3u) * 4 + kFusedTileBits / 8;
+    auto k = k_seg_cover<NT, NB>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT, smem, s>>>(a, sv, off_w);
+    return cudaGetLastError();
+}
+
+uint32_t seg_cover_offset(uint32_t H, uint32_t P1)
+{
+    const uint32_t bits = P1 + 1 < H ? (H - P1 - 1) / 2 : 0;
+    return bits >= 64 ? bits / 32 - 1 : 0;
+}
+
+cudaError_t launch_seg_cover(const CoverArgs& a, const SieveArgs& sv, int KA, uint32_t P1, cudaStream_t s)
+{
+    // the tile must hold the chunk's words and the partner halo read past
+    // them, from the offset of the pass's largest prime on
+    const uint32_t off_w = seg_cover_offset(a.H, P1);
+    const uint64_t need_words = 2ull * a.cta_words + ((a.H - 4) >> 6) + 3 - off_w;
+    if (need_words * 32 > kFusedTileBits || sv.tile_bits != kFusedTileBits || sv.out || sv.popcount)
+        return cudaErrorInvalidValue;
+    if (2ull * a.cta_words > 10ull * 768) return cudaErrorInvalidValue;
+    switch (KA) {
+    case 64: return launch_seg_nb<1>(a, sv, off_w, s);
+    case 128: return launch_seg_nb<2>(a, sv, off_w, s);
+    case 192: return launch_seg_nb<3>(a, sv, off_w, s);
+    case 256: return launch_seg_nb<4>(a, sv, off_w, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // persistent: CTAs take (range, chunk) items from the queue until it is empty;
@@ -522,7 +606,8 @@ __global__ void __launch_bounds__(NT, 4) k_cover_items(const CoverItemsArgs a)
         uint64_t w_end = w_begin + 2ull * c.cta_words;
         const uint64_t nw32 = (r.n + 31) / 32;
         if (w_end > nw32) w_end = nw32;
-        cover_chunk<NT, NB>(c, ri, w_begin, w_end, (uint32_t)(32 * w_begin), smem, shist, smax);
+        cover_chunk<NT, NB, false>(c, reinterpret_cast<const uint32_t*>(c.Q) + w_begin, ri, w_begin, w_end,
+                                   (uint32_t)(32 * w_begin), smem, shist, smax);
     }
 }
 

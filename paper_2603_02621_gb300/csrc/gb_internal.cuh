@@ -151,6 +151,13 @@ cudaError_t launch_cover(const CoverArgs& a, int threads, cudaStream_t s);
 int cover_fast_phase_primes(uint32_t K, uint64_t n_hi);   // KA for K primes near n_hi (0: none)
 cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s);
 
+// Sieve and block cover fused per CTA (k_seg_cover): the window is sieved
+// tile by tile into shared memory (sv.out and sv.popcount null, sv.tile_bits
+// == kFusedTileBits, no primes above the split) and covered there.
+constexpr uint32_t kFusedTileBits = (1u << 18) + 8192;
+uint32_t seg_cover_offset(uint32_t H, uint32_t P1);     // first window word the cover reads, per chunk
+cudaError_t launch_seg_cover(const CoverArgs& a, const SieveArgs& sv, int KA, uint32_t P1, cudaStream_t s);
+
 struct RetryArgs {
     const uint64_t* Q;
     uint32_t H;
