@@ -155,6 +155,7 @@ struct gb_ctx {
     // are struck by global atomics, measured faster on GB300
     bool bucket_large = false;
     bool fused = false;               // sieve and block cover fused per CTA (GB_FUSED=1)
+    uint32_t mid_limit = 1u << 20;    // primes from the split below this: per 2^20-bit slice (GB_MID_LOG2; 0 = off)
     uint32_t fill_grid = 0;           // persistent fill CTAs
     uint32_t bcap = 0;                // entries per (CTA, bucket tile) list
     uint64_t bucket_overflows = 0;    // chunks redone by the atomic kernel
@@ -350,10 +351,23 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
         la.n_primes = (uint32_t)(np - nsmall);
         la.out = out;
         la.strikes = ctx->work_ptr(2);
+        // primes below mid_limit: per 2^20-bit slice in shared memory
+        uint64_t nmid = nsmall;
+        if (ctx->mid_limit > ctx->cfg.bucket_split) {
+            nmid = std::min<uint64_t>(np, std::max<uint64_t>(nsmall, ctx->pi(ctx->mid_limit - 1)));
+            if (nmid > nsmall) {
+                gb::LargeArgs ma = la;
+                ma.n_primes = (uint32_t)(nmid - nsmall);
+                GB_LAUNCH(gb::launch_mid(ma, nbits, ctx->stream));
+            }
+            la.primes = ctx->base->primes.as<uint32_t>() + nmid;
+            la.recip = ctx->base->recip.as<uint64_t>() + nmid;
+            la.n_primes = (uint32_t)(np - nmid);
+        }
         // primes of at least a bucket tile (2^20) go to the bucket sieve; those
         // between the split and a bucket tile hit a tile several times and
         // keep the atomic kernel
-        const uint64_t nbucket_lo = ctx->bucket_large ? std::max<uint64_t>(nsmall, ctx->pi((1u << gb::kBucketTileLog2) - 1)) : np;
+        const uint64_t nbucket_lo = ctx->bucket_large ? std::max<uint64_t>(nmid, ctx->pi((1u << gb::kBucketTileLog2) - 1)) : np;
         if (nbucket_lo < np) {
             // bucket sieve, chunk by chunk of at most 2^30 bits; a chunk whose
             // lists overflowed is struck again by the atomic kernel below
@@ -400,8 +414,8 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
                 GB_LAUNCH(gb::launch_large(lb, ctx->stream));
             }
         }
-        if (nbucket_lo > nsmall) {
-            la.n_primes = (uint32_t)(nbucket_lo - nsmall);
+        if (nbucket_lo > nmid) {
+            la.n_primes = (uint32_t)(nbucket_lo - nmid);
             const uint64_t chunk = ctx->large_chunk_bits;
             for (uint64_t c0 = 0; c0 < nbits; c0 += chunk) {
                 la.bit_lo = c0;
@@ -576,6 +590,10 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     if (const char* e = getenv("GB_BATCH_GRAPH")) ctx->batch_graph = atoi(e) != 0;
     if (const char* e = getenv("GB_LARGE")) ctx->bucket_large = std::string(e) == "bucket";
     if (const char* e = getenv("GB_FUSED")) ctx->fused = atoi(e) != 0;
+    if (const char* e = getenv("GB_MID_LOG2")) {
+        const int v = atoi(e);
+        ctx->mid_limit = (v >= 16 && v <= 31) ? (1u << v) : 0u;
+    }
     if (const char* e = getenv("GB_LARGE_CHUNK_LOG2")) {
         const int v = atoi(e);
         if (v >= 16 && v <= 40) ctx->large_chunk_bits = 1ull << v;
@@ -612,6 +630,7 @@ int gb_init_shared(gb_ctx** out, const gb_ctx* parent, void* stream)
     ctx->large_chunk_bits = parent->large_chunk_bits;
     ctx->bucket_large = parent->bucket_large;
     ctx->fused = parent->fused;
+    ctx->mid_limit = parent->mid_limit;
     *out = ctx;
     return GB_OK;
 }
@@ -1011,12 +1030,25 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
         groups.push_back(count);
     }
     const uint32_t n_groups = (uint32_t)groups.size() - 1;
-    if (np > nsmall && (uint64_t)n_groups * ((np - nsmall + 255) / 256) > 0xffffffffull)
+    // primes from the split below the mid limit: per 2^20-bit slice of each
+    // range's window, in shared memory; the rest by the large-prime queue
+    const uint64_t nmid = ctx->mid_limit > cfg.bucket_split
+                              ? std::min<uint64_t>(np, std::max<uint64_t>(nsmall, ctx->pi(ctx->mid_limit - 1)))
+                              : nsmall;
+    uint64_t n_mid = 0;
+    if (nmid > nsmall)
+        for (uint32_t i = 0; i < count; ++i) {
+            const uint64_t qw = (hi[i] - lo[i]) / 2 / 64 + 1 + H / 128 + 2;
+            n_mid += (64 * qw + (1ull << gb::kMidSliceLog2) - 1) >> gb::kMidSliceLog2;
+        }
+    if (np > nmid && (uint64_t)n_groups * ((np - nmid + 255) / 256) > 0xffffffffull)
         return fail(GB_EINVAL, "batch too large");
+    if (n_mid > 0xffffffffull) return fail(GB_EINVAL, "batch too large");
 
     // device buffers
     const size_t desc_ranges = (size_t)count * sizeof(gb::BatchRange);
-    const size_t desc_bytes = desc_ranges + (size_t)(2 * n_sieve + 2 * n_cover) * 4 + (size_t)(n_groups + 1) * 4 + 64;
+    const size_t desc_bytes = desc_ranges + (size_t)(2 * n_sieve + 2 * n_cover + 2 * n_mid) * 4 +
+                              (size_t)(n_groups + 1) * 4 + 64;
     const bool want_rows = hist && hist_stride;
     const bool res_dev = is_device_ptr(results);
     const bool rows_dev = want_rows && is_device_ptr(hist);
@@ -1037,9 +1069,12 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     uint32_t* c_range = s_tile + n_sieve;
     uint32_t* c_chunk = c_range + n_cover;
     uint32_t* g_first = c_chunk + n_cover;
-    uint32_t* counts = g_first + n_groups + 1;               // [0] sieve items, [1] cover items, [2] ranges
+    uint32_t* m_range = g_first + n_groups + 1;
+    uint32_t* m_slice = m_range + n_mid;
+    // [0] sieve items, [1] cover items, [2] ranges, [3] large-prime items, [4] mid items
+    uint32_t* counts = m_slice + n_mid;
     {
-        uint64_t off = 0, si = 0, ci = 0;
+        uint64_t off = 0, si = 0, ci = 0, mi = 0;
         for (uint32_t i = 0; i < count; ++i) {
             const uint64_t n = (hi[i] - lo[i]) / 2;
             const uint64_t qw = (n + 63) / 64 + H / 128 + 2;
@@ -1053,15 +1088,20 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
             for (uint64_t t = 0; t < tiles; ++t) { s_range[si] = i; s_tile[si] = (uint32_t)t; ++si; }
             const uint64_t chunks = (((n + 31) / 32) + 2ull * cw - 1) / (2ull * cw);
             for (uint64_t c = 0; c < chunks; ++c) { c_range[ci] = i; c_chunk[ci] = (uint32_t)c; ++ci; }
+            if (n_mid) {
+                const uint64_t slices = (64 * qw + (1ull << gb::kMidSliceLog2) - 1) >> gb::kMidSliceLog2;
+                for (uint64_t t = 0; t < slices; ++t) { m_range[mi] = i; m_slice[mi] = (uint32_t)t; ++mi; }
+            }
         }
         for (uint32_t g = 0; g <= n_groups; ++g) g_first[g] = groups[g];
         counts[0] = (uint32_t)n_sieve;
         counts[1] = (uint32_t)n_cover;
         counts[2] = count;
-        counts[3] = np > nsmall ? (uint32_t)(n_groups * ((np - nsmall + 255) / 256)) : 0u;
+        counts[3] = np > nmid ? (uint32_t)(n_groups * ((np - nmid + 255) / 256)) : 0u;
+        counts[4] = (uint32_t)mi;
     }
     unsigned char* dd = static_cast<unsigned char*>(ctx->bdesc.p);
-    const size_t used = reinterpret_cast<unsigned char*>(counts + 4) - hs_p;
+    const size_t used = reinterpret_cast<unsigned char*>(counts + 5) - hs_p;
     GB_CUDA(cudaMemcpyAsync(dd, hs_p, used, cudaMemcpyHostToDevice, s));
     const gb::BatchRange* d_ranges = reinterpret_cast<const gb::BatchRange*>(dd);
     const uint32_t* d_s_range = reinterpret_cast<const uint32_t*>(dd + desc_ranges);
@@ -1069,7 +1109,9 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     const uint32_t* d_c_range = d_s_tile + n_sieve;
     const uint32_t* d_c_chunk = d_c_range + n_cover;
     const uint32_t* d_groups = d_c_chunk + n_cover;
-    const uint32_t* d_counts = d_groups + n_groups + 1;
+    const uint32_t* d_m_range = d_groups + n_groups + 1;
+    const uint32_t* d_m_slice = d_m_range + n_mid;
+    const uint32_t* d_counts = d_m_slice + n_mid;
 
     unsigned int* heads = ctx->counter.as<unsigned int>();
     GB_CUDA(cudaMemsetAsync(heads, 0, 16, s));
@@ -1122,14 +1164,28 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
             la.groups = d_groups;
             la.n_items = d_counts + 3;
             la.head = heads + 2;
-            la.primes = ctx->base->primes.as<uint32_t>() + nsmall;
-            la.recip = ctx->base->recip.as<uint64_t>() + nsmall;
-            la.n_primes = (uint32_t)(np - nsmall);
+            la.primes = ctx->base->primes.as<uint32_t>() + nmid;
+            la.recip = ctx->base->recip.as<uint64_t>() + nmid;
+            la.n_primes = (uint32_t)(np - nmid);
             la.Q = ctx->bq.as<uint32_t>();
             la.strikes = ctx->work_ptr(2);
             ctx->prof_end();
             ctx->prof_begin(kProfLarge, qwords * 64);
-            if (np > nsmall) GB_LAUNCH(gb::launch_large_batch(la, ls));
+            if (nmid > nsmall) {
+                gb::MidItemsArgs ma{};
+                ma.ranges = d_ranges;
+                ma.item_range = d_m_range;
+                ma.item_slice = d_m_slice;
+                ma.n_items = d_counts + 4;
+                ma.head = heads + 3;
+                ma.primes = ctx->base->primes.as<uint32_t>() + nsmall;
+                ma.recip = ctx->base->recip.as<uint64_t>() + nsmall;
+                ma.n_primes = (uint32_t)(nmid - nsmall);
+                ma.Q = ctx->bq.as<uint32_t>();
+                ma.strikes = ctx->work_ptr(2);
+                GB_LAUNCH(gb::launch_mid_items(ma, ls));
+            }
+            if (np > nmid) GB_LAUNCH(gb::launch_large_batch(la, ls));
         }
         ctx->prof_end();
 

@@ -87,6 +87,12 @@ struct LargeArgs {
     unsigned long long* strikes;    // optional work count
 };
 cudaError_t launch_large(const LargeArgs& a, cudaStream_t s);
+// the same primes struck per 2^20-bit slice of the window in shared memory
+// (one Barrett start per prime and slice): for primes up to a few slices,
+// whose strikes are dense enough to pay for the starts (LargeArgs: bit_lo /
+// bit_hi unused, the whole window)
+constexpr uint32_t kMidSliceLog2 = 20;
+cudaError_t launch_mid(const LargeArgs& a, uint64_t nbits, cudaStream_t s);
 // population count of n 32-bit words, added to *count
 cudaError_t launch_popcount(const uint32_t* words, uint64_t n, unsigned long long* count, cudaStream_t s);
 
@@ -260,6 +266,22 @@ struct CoverItemsArgs {
     const uint64_t* Q;          // batch buffer
 };
 cudaError_t launch_cover_items(const CoverItemsArgs& a, int KA, cudaStream_t s);
+
+// primes from the split below the mid limit over (range, 2^20-bit slice)
+// items of a batch, in shared memory
+struct MidItemsArgs {
+    const BatchRange* ranges;
+    const uint32_t* item_range;
+    const uint32_t* item_slice;
+    const uint32_t* n_items;    // device
+    unsigned int* head;         // device queue head (zeroed)
+    const uint32_t* primes;
+    const uint64_t* recip;
+    uint32_t n_primes;
+    uint32_t* Q;                // batch buffer (32-bit words)
+    unsigned long long* strikes;
+};
+cudaError_t launch_mid_items(const MidItemsArgs& a, cudaStream_t s);
 
 // large primes over groups of ranges (a group's windows together fit in L2):
 // items (group, block of 256 primes), group-major, from a device queue

@@ -212,6 +212,105 @@ cudaError_t launch_large(const LargeArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Primes between the tile split and a few 2^20-bit slices: each CTA loads one
+// slice of the window (already sieved by the smaller primes) into shared
+// memory, strikes every such prime in it (one Barrett start per prime and
+// slice), and stores it back -- shared-memory atomics instead of one L2
+// request per strike.
+__device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* words, uint64_t t0,
+                                          const uint32_t* primes, const uint64_t* recip, uint32_t n_primes,
+                                          uint32_t* slice, unsigned long long& nstrike)
+{
+    const uint64_t rem = nbits - t0;
+    const uint32_t nb = rem < (1ull << kMidSliceLog2) ? (uint32_t)rem : (1u << kMidSliceLog2);
+    const uint32_t nw = (nb + 31) / 32;
+    uint32_t* q = words + t0 / 32;
+    __syncthreads();                                          // slice free
+    for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) slice[w] = q[w];
+    __syncthreads();
+    const int64_t b = B + 2 * (int64_t)t0;
+    const int64_t last = B + 2 * (int64_t)(t0 + nb - 1);
+    for (uint32_t k = threadIdx.x; k < n_primes; k += blockDim.x) {
+        const uint32_t p = primes[k];
+        const uint64_t pp = (uint64_t)p * p;
+        if ((int64_t)pp > last) break;                       // ascending primes
+        uint32_t i = first_odd_multiple(b, p, recip[k]);
+        if ((int64_t)pp > b) {
+            const uint64_t isq = ((uint64_t)((int64_t)pp - b)) >> 1;
+            if (isq > i) i = (uint32_t)isq;                   // isq < nb here
+        }
+        for (; i < nb; i += p) {                              // p < 2^31, i < 2^20: no wrap
+            atomicAnd(slice + (i >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, i));
+            ++nstrike;
+        }
+    }
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) q[w] = slice[w];
+}
+
+__global__ void __launch_bounds__(1024) k_mid(const LargeArgs a, uint64_t nbits)
+{
+    extern __shared__ uint32_t slice[];
+    unsigned long long nstrike = 0;
+    mid_slice(a.B, nbits, a.out, (uint64_t)blockIdx.x << kMidSliceLog2, a.primes, a.recip, a.n_primes, slice,
+              nstrike);
+    if (a.strikes) {
+        for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);
+        if ((threadIdx.x & 31) == 0 && nstrike) atomicAdd(a.strikes, nstrike);
+    }
+}
+
+// batched: persistent CTAs take (range, slice) items from a device queue
+__global__ void __launch_bounds__(1024) k_mid_items(const MidItemsArgs a)
+{
+    extern __shared__ uint32_t slice[];
+    __shared__ uint32_t s_item;
+    const uint32_t n_items = *a.n_items;
+    unsigned long long nstrike = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.head, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        const BatchRange r = a.ranges[a.item_range[item]];
+        mid_slice(r.B, r.nbits, a.Q + 2 * r.q_off, (uint64_t)a.item_slice[item] << kMidSliceLog2, a.primes, a.recip,
+                  a.n_primes, slice, nstrike);
+    }
+    if (a.strikes) {
+        for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);
+        if ((threadIdx.x & 31) == 0 && nstrike) atomicAdd(a.strikes, nstrike);
+    }
+}
+
+cudaError_t launch_mid_items(const MidItemsArgs& a, cudaStream_t s)
+{
+    if (a.n_primes == 0) return cudaSuccess;
+    if (!a.primes || !a.recip || !a.Q || !a.ranges || !a.item_range || !a.item_slice || !a.n_items || !a.head)
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(1u << kMidSliceLog2) / 8;
+    cudaError_t e = cudaFuncSetAttribute(k_mid_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    k_mid_items<<<(unsigned)sms, 1024, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mid(const LargeArgs& a, uint64_t nbits, cudaStream_t s)
+{
+    if (a.n_primes == 0 || nbits == 0) return cudaSuccess;
+    if (!a.primes || !a.recip || !a.out) return cudaErrorInvalidValue;
+    const uint64_t slices = (nbits + (1ull << kMidSliceLog2) - 1) >> kMidSliceLog2;
+    if (slices > 0x7fffffffull) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(1u << kMidSliceLog2) / 8;
+    cudaError_t e = cudaFuncSetAttribute(k_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_mid<<<(unsigned)slices, 1024, smem, s>>>(a, nbits);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_popcount(const uint32_t* w, uint64_t n, unsigned long long* count)
 {
     unsigned long long c = 0;
