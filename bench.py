@@ -432,6 +432,9 @@ def run_serving(args, gb, torch, world, rank, local, backend_ready):
             st = srv.stats()
         return out, wall, st
 
+    # the lanes copy the context's configuration: tune it on a sample stream first
+    sample = [(a, b) for t, kind, a, b in workloads.serving_stream(count=160, seed=1000 + rank) if kind == "range"]
+    tuned, tune_ms = ctx.autotune(sample, gb.GB_TUNE_BATCH, reps=1)
     serve(workloads.serving_stream(count=200, seed=1000 + rank), args.lanes)       # warm-up, arenas
     reqs = workloads.serving_stream(count=args.requests, seed=7 + rank)
     clocks = ClockSampler(local)
@@ -472,6 +475,7 @@ def run_serving(args, gb, torch, world, rank, local, backend_ready):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 16 * (len(reqs) - n_q) + 8 * n_q,
                     "d2h_bytes_per_step": 48 * (len(reqs) - n_q) + 4 * n_q},
             "clocks": clk, "gpu_launches": None, "server": st, "failed_requests": len(bad),
+            "autotuned": {k: tuned[k] for k in ("tile_bits", "bucket_split", "p1", "cover_prefix")},
             "wall_s": wall, "paper_context": PAPER_CONTEXT}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -1012,26 +1012,11 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     if (isqrt_u64(last_max) > ctx->L) return fail(GB_EINVAL, "hi beyond base_limit^2");
     if (n_sieve > 0xffffffffull || n_cover > 0xffffffffull) return fail(GB_EINVAL, "batch too large");
 
-    // large primes and their groups of ranges (windows of a group fit in L2)
+    // large primes: np primes <= sqrt of the batch's last number; those below
+    // the split strike per tile, those below the mid limit per 2^20-bit slice
+    // of each window in shared memory, the rest per window piece by atomics
     const uint64_t np = ctx->pi(isqrt_u64(last_max));
     const uint64_t nsmall = std::min<uint64_t>(np, std::max<uint64_t>(ctx->pi(cfg.bucket_split - 1), gb::kFirstStrikeIdx));
-    std::vector<uint32_t> groups;
-    {
-        uint64_t acc = 0;
-        groups.push_back(0);
-        for (uint32_t i = 0; i < count; ++i) {
-            const uint64_t qb = 64 * ((hi[i] - lo[i]) / 2 / 64 + H / 128 + 3);
-            if (acc && acc + qb > ctx->large_chunk_bits) {
-                groups.push_back(i);
-                acc = 0;
-            }
-            acc += qb;
-        }
-        groups.push_back(count);
-    }
-    const uint32_t n_groups = (uint32_t)groups.size() - 1;
-    // primes from the split below the mid limit: per 2^20-bit slice of each
-    // range's window, in shared memory; the rest by the large-prime queue
     const uint64_t nmid = ctx->mid_limit > cfg.bucket_split
                               ? std::min<uint64_t>(np, std::max<uint64_t>(nsmall, ctx->pi(ctx->mid_limit - 1)))
                               : nsmall;
@@ -1041,12 +1026,48 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
             const uint64_t qw = (hi[i] - lo[i]) / 2 / 64 + 1 + H / 128 + 2;
             n_mid += (64 * qw + (1ull << gb::kMidSliceLog2) - 1) >> gb::kMidSliceLog2;
         }
-    if (np > nmid && (uint64_t)n_groups * ((np - nmid + 255) / 256) > 0xffffffffull)
-        return fail(GB_EINVAL, "batch too large");
     if (n_mid > 0xffffffffull) return fail(GB_EINVAL, "batch too large");
+    // window pieces of at most one L2-sized chunk, grouped up to a chunk;
+    // within a group by their prime counts, descending
+    std::vector<gb::LargePiece> pieces;
+    std::vector<uint32_t> groups;
+    uint32_t nblk = 0;
+    if (np > nmid) {
+        const uint64_t chunk = ctx->large_chunk_bits;
+        uint64_t acc = 0;
+        uint32_t most = 0;
+        groups.push_back(0);
+        for (uint32_t i = 0; i < count; ++i) {
+            const uint64_t nb = 64 * ((hi[i] - lo[i]) / 2 / 64 + (((hi[i] - lo[i]) / 2) % 64 ? 1 : 0) + H / 128 + 2);
+            const int64_t Bi = (int64_t)lo[i] - (int64_t)H + 1;
+            for (uint64_t b0 = 0; b0 < nb; b0 += chunk) {
+                const uint64_t b1 = std::min(nb, b0 + chunk);
+                const int64_t lastn = Bi + 2 * (int64_t)(b1 - 1);
+                const uint64_t npc = lastn > 0 ? ctx->pi(isqrt_u64((uint64_t)lastn)) : 0;
+                const uint32_t nl = npc > nmid ? (uint32_t)(npc - nmid) : 0u;
+                if (!nl) continue;
+                if (acc && acc + (b1 - b0) > chunk) {
+                    groups.push_back((uint32_t)pieces.size());
+                    acc = 0;
+                }
+                pieces.push_back(gb::LargePiece{i, nl, b0, b1});
+                acc += b1 - b0;
+                most = std::max(most, nl);
+            }
+        }
+        groups.push_back((uint32_t)pieces.size());
+        for (size_t g = 0; g + 1 < groups.size(); ++g)
+            std::stable_sort(pieces.begin() + groups[g], pieces.begin() + groups[g + 1],
+                             [](const gb::LargePiece& x, const gb::LargePiece& y) { return x.n_primes > y.n_primes; });
+        nblk = (most + 255) / 256;
+    }
+    const uint64_t n_pieces = pieces.size();
+    const uint32_t n_groups = groups.empty() ? 0u : (uint32_t)groups.size() - 1;
+    const uint64_t n_large_items = (uint64_t)n_groups * nblk;
+    if (n_large_items > 0xffffffffull) return fail(GB_EINVAL, "batch too large");
 
     // device buffers
-    const size_t desc_ranges = (size_t)count * sizeof(gb::BatchRange);
+    const size_t desc_ranges = (size_t)count * sizeof(gb::BatchRange) + n_pieces * sizeof(gb::LargePiece);
     const size_t desc_bytes = desc_ranges + (size_t)(2 * n_sieve + 2 * n_cover + 2 * n_mid) * 4 +
                               (size_t)(n_groups + 1) * 4 + 64;
     const bool want_rows = hist && hist_stride;
@@ -1061,9 +1082,12 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
         (rc = ctx->counter.ensure(16)))
         return rc;
 
-    // descriptors, staged in pinned memory: ranges | sieve items | cover items | groups | counts
+    // descriptors, staged in pinned memory: ranges | pieces | sieve items |
+    // cover items | piece groups | mid items | counts
     unsigned char* hs_p = static_cast<unsigned char*>(ctx->hstage.p);
     gb::BatchRange* hr = reinterpret_cast<gb::BatchRange*>(hs_p);
+    gb::LargePiece* hpc = reinterpret_cast<gb::LargePiece*>(hs_p + (size_t)count * sizeof(gb::BatchRange));
+    std::memcpy(hpc, pieces.data(), n_pieces * sizeof(gb::LargePiece));
     uint32_t* s_range = reinterpret_cast<uint32_t*>(hs_p + desc_ranges);
     uint32_t* s_tile = s_range + n_sieve;
     uint32_t* c_range = s_tile + n_sieve;
@@ -1093,17 +1117,18 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
                 for (uint64_t t = 0; t < slices; ++t) { m_range[mi] = i; m_slice[mi] = (uint32_t)t; ++mi; }
             }
         }
-        for (uint32_t g = 0; g <= n_groups; ++g) g_first[g] = groups[g];
         counts[0] = (uint32_t)n_sieve;
         counts[1] = (uint32_t)n_cover;
         counts[2] = count;
-        counts[3] = np > nmid ? (uint32_t)(n_groups * ((np - nmid + 255) / 256)) : 0u;
+        for (uint32_t g = 0; g < n_groups + (n_groups ? 1u : 0u); ++g) g_first[g] = groups[g];
+        counts[3] = (uint32_t)n_large_items;
         counts[4] = (uint32_t)mi;
     }
     unsigned char* dd = static_cast<unsigned char*>(ctx->bdesc.p);
     const size_t used = reinterpret_cast<unsigned char*>(counts + 5) - hs_p;
     GB_CUDA(cudaMemcpyAsync(dd, hs_p, used, cudaMemcpyHostToDevice, s));
     const gb::BatchRange* d_ranges = reinterpret_cast<const gb::BatchRange*>(dd);
+    const gb::LargePiece* d_pieces = reinterpret_cast<const gb::LargePiece*>(dd + (size_t)count * sizeof(gb::BatchRange));
     const uint32_t* d_s_range = reinterpret_cast<const uint32_t*>(dd + desc_ranges);
     const uint32_t* d_s_tile = d_s_range + n_sieve;
     const uint32_t* d_c_range = d_s_tile + n_sieve;
@@ -1161,7 +1186,9 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
         {
             gb::LargeBatchArgs la{};
             la.ranges = d_ranges;
+            la.pieces = d_pieces;
             la.groups = d_groups;
+            la.nblk = nblk;
             la.n_items = d_counts + 3;
             la.head = heads + 2;
             la.primes = ctx->base->primes.as<uint32_t>() + nmid;
@@ -1185,7 +1212,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
                 ma.strikes = ctx->work_ptr(2);
                 GB_LAUNCH(gb::launch_mid_items(ma, ls));
             }
-            if (np > nmid) GB_LAUNCH(gb::launch_large_batch(la, ls));
+            if (n_pieces) GB_LAUNCH(gb::launch_large_batch(la, ls));
         }
         ctx->prof_end();
 

@@ -12,13 +12,13 @@ namespace gb {
 
 // primes above the tile size: persistent CTAs take (group, block of 256
 // primes) items in group-major order, so the CTAs work on one or two groups at
-// a time and the struck words stay in L2; one thread per prime, every range
-// of the group
+// a time and the struck words stay in L2; one thread per prime, over the
+// pieces of the group in descending order of their prime counts, stopping at
+// the first piece its prime does not reach (p^2 beyond the piece's end).
 __global__ void __launch_bounds__(256) k_large_batch(const LargeBatchArgs a)
 {
     __shared__ uint32_t s_item;
     const uint32_t n_items = *a.n_items;
-    const uint32_t nblk = (a.n_primes + 255) / 256;
     unsigned long long nstrike = 0;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.head, 1u);
@@ -26,25 +26,28 @@ __global__ void __launch_bounds__(256) k_large_batch(const LargeBatchArgs a)
         const uint32_t item = s_item;
         __syncthreads();
         if (item >= n_items) break;
-        const uint32_t g = item / nblk;
-        const uint32_t k = (item - g * nblk) * 256 + threadIdx.x;
-        if (k >= a.n_primes) continue;
-        const uint32_t r0 = a.groups[g], r1 = a.groups[g + 1];
+        const uint32_t g = item / a.nblk;
+        const uint32_t k = (item - g * a.nblk) * 256 + threadIdx.x;
+        const uint32_t g0 = a.groups[g], g1 = a.groups[g + 1];
+        if (g0 == g1 || k >= a.pieces[g0].n_primes) continue;
         const uint32_t p = a.primes[k];
         const uint64_t m = a.recip[k];
         const uint64_t pp = (uint64_t)p * p;
-        for (uint32_t ri = r0; ri < r1; ++ri) {
-            const BatchRange r = a.ranges[ri];
-            const int64_t last = r.B + 2 * (int64_t)(r.nbits - 1);
+        for (uint32_t pi = g0; pi < g1; ++pi) {
+            const LargePiece pc = a.pieces[pi];
+            if (k >= pc.n_primes) break;                                   // and every later piece
+            const BatchRange r = a.ranges[pc.range];
+            const int64_t b = r.B + 2 * (int64_t)pc.bit_lo;               // number at the piece's first bit
+            const int64_t last = r.B + 2 * (int64_t)(pc.bit_hi - 1);
             if ((int64_t)pp > last) continue;
-            uint64_t i = first_odd_multiple(r.B, p, m);
-            if ((int64_t)pp > r.B) {
-                const uint64_t isq = ((uint64_t)((int64_t)pp - r.B)) >> 1;
+            uint64_t i = first_odd_multiple(b, p, m);
+            if ((int64_t)pp > b) {
+                const uint64_t isq = ((uint64_t)((int64_t)pp - b)) >> 1;
                 if (isq > i) i = isq;
             }
             uint32_t* q = a.Q + 2 * r.q_off;
-            for (; i < r.nbits; i += p) {
-                atomicAnd(q + (i >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, (uint32_t)i));
+            for (uint64_t bit = pc.bit_lo + i; bit < pc.bit_hi; bit += p) {
+                atomicAnd(q + (bit >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, (uint32_t)bit));
                 ++nstrike;
             }
         }
@@ -58,6 +61,8 @@ __global__ void __launch_bounds__(256) k_large_batch(const LargeBatchArgs a)
 cudaError_t launch_large_batch(const LargeBatchArgs& a, cudaStream_t s)
 {
     if (a.n_primes == 0) return cudaSuccess;
+    if (!a.ranges || !a.pieces || !a.groups || a.nblk == 0 || !a.n_items || !a.head || !a.primes || !a.recip || !a.Q)
+        return cudaErrorInvalidValue;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

@@ -283,12 +283,22 @@ struct MidItemsArgs {
 };
 cudaError_t launch_mid_items(const MidItemsArgs& a, cudaStream_t s);
 
-// large primes over groups of ranges (a group's windows together fit in L2):
-// items (group, block of 256 primes), group-major, from a device queue
+// large primes over groups of window pieces (a group's pieces together fit in
+// L2; a long window is cut into several pieces): items (group, block of 256
+// primes), group-major, from a device queue; a thread stops at the first
+// piece of its group that its prime does not reach
+// a run of one range's window bits, at most an L2-sized chunk
+struct LargePiece {
+    uint32_t range;
+    uint32_t n_primes;          // large primes with p^2 <= the piece's last number
+    uint64_t bit_lo, bit_hi;
+};
 struct LargeBatchArgs {
     const BatchRange* ranges;
-    const uint32_t* groups;     // device: first range of each group, then the count
-    const uint32_t* n_items;    // device: groups x prime blocks
+    const LargePiece* pieces;   // grouped; within a group by n_primes, descending
+    const uint32_t* groups;     // device: first piece of each group, then the count
+    uint32_t nblk;              // blocks of 256 primes per group (the most any piece needs)
+    const uint32_t* n_items;    // device: groups x nblk
     unsigned int* head;         // device queue head (zeroed)
     const uint32_t* primes;     // the large primes
     const uint64_t* recip;
