@@ -150,7 +150,7 @@ int gb_get_config(const gb_ctx* ctx, gb_config* out);
  * histogram length follows p1. */
 int gb_set_config(gb_ctx* ctx, const gb_config* cfg);
 
-/* Autotuner (the batched configuration's "autotuned segment / tile / CTA / P"):
+/* Autotuner (segment length, sieve tile, CTA size, tile / large-prime split, P):
  * verifies the sample workload [lo[i], hi[i]) i < count under candidate
  * settings, one parameter at a time (coordinate descent over tile_bits,
  * bucket_split, p1, cover_prefix and, for GB_TUNE_PLAIN, seg_len and

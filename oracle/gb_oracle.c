@@ -9,13 +9,13 @@
  * Everything here is the plain definition written out, slowly and obviously:
  *
  *   * a prime flag is one byte per INTEGER (evens included), produced by the
- *     sieve of Eratosthenes (Sec. 2.1: "a segmented Sieve of Eratosthenes
- *     generates all primes up to N");
- *   * p_min(n) = min { p prime : n - p prime } for even n >= 4 (Sec. 2.1: for
- *     each even n "scans primes p from 2 ... and checks whether q = n - p is
- *     prime"; Sec. 2.3.2 names the minimal Goldbach prime and its envelope);
- *     the scan below tries p = 2, 3, 5, ... in ascending order, p <= P, and
- *     stops at the first prime whose partner is prime;
+ *     sieve of Eratosthenes (Sec. 2.1: the CPU baseline sieves the primes up
+ *     to N first);
+ *   * p_min(n) = min { p prime : n - p prime } for even n >= 4 (Sec. 2.1: the
+ *     baseline walks the primes upward from 2 for each even n and tests the
+ *     partner n - p; Sec. 2.3.2 names the minimal Goldbach prime and its
+ *     envelope); the scan below tries p = 2, 3, 5, ... in ascending order,
+ *     p <= P, and stops at the first prime whose partner is prime;
  *   * the per-segment outputs (histogram of p_min over prime index, the largest
  *     p_min with the smallest n attaining it, the count of n with no p <= P)
  *     are accumulated from those per-n values (Sec. 2.3.2 Phase 1, the
