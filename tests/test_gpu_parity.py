@@ -99,7 +99,7 @@ def test_prime_pi(gbm, x, pi):
 
 # ------------------------------------------------------------------ cover
 
-def test_config1_pmin_array(gbm, oracle):
+def test_pmin_array_4_to_1e7(gbm, oracle):
     """Every even n in [4, 10^7], one segment, P = 2^16: the full p_min array."""
     lo, hi, P = 4, 10**7 + 2, 1 << 16
     S = ((5 * 10**6 + 2047) // 2048) * 2048
@@ -117,7 +117,7 @@ def test_config1_pmin_array(gbm, oracle):
     assert np.array_equal(r["hist"], hist[0])
 
 
-def test_config2_full(gbm, oracle):
+def test_exhaustive_4_to_1e10_full(gbm, oracle):
     """Exhaustive [4, 10^10]: segments of 2^24, base primes to 10^5, P1 = 2^15
     with a GPU retry pass to 2^20; per-segment histogram, max, unresolved."""
     lo, hi = 4, 10**10 + 2
