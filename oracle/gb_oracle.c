@@ -364,6 +364,38 @@ uint64_t or_td_pmin(uint64_t n)
 }
 
 /* number of Goldbach partitions c(n) = #{ p <= n/2 : p and n - p prime } */
+/* ------------------------------------------------------------------------ */
+/* sieve work: the strikes a segmented sieve makes in a window                 */
+/* ------------------------------------------------------------------------ */
+/* For the odd numbers a_odd, a_odd + 2, ..., a_odd + 2 (nbits - 1): the number
+ * of pairs (p, m) with p a prime in [p_lo, p_hi], p^2 <= the window's last
+ * number, and m an odd multiple of p in the window with m >= p^2 -- each
+ * composite struck once per prime factor in that range, as the sieve of
+ * Eratosthenes of Sec. 2.1 crosses out from p^2 on.  Counted per prime as the
+ * odd j with max(p^2, a_odd) <= p j <= last. */
+uint64_t or_count_strikes(int64_t a_odd, uint64_t nbits, uint64_t p_lo, uint64_t p_hi)
+{
+    if (nbits == 0) return 0;
+    const int64_t last = a_odd + 2 * (int64_t)(nbits - 1);
+    if (last < 4) return 0;
+    const uint64_t r = or_isqrt((uint64_t)last);
+    if (p_hi > r) p_hi = r;
+    if (ensure_small(p_hi < 16 ? 16 : p_hi)) return 0;
+    uint64_t total = 0;
+    for (uint64_t k = 0; k < g_nsmall && g_small[k] <= p_hi; k++) {
+        const uint64_t p = g_small[k];
+        if (p < p_lo || p == 2) continue;
+        uint64_t L = p * p;
+        if (a_odd > 0 && (uint64_t)a_odd > L) L = (uint64_t)a_odd;
+        const uint64_t jlo = (L + p - 1) / p, jhi = (uint64_t)last / p;
+        if (jhi < jlo) continue;
+        /* odd j in [jlo, jhi] */
+        const uint64_t first = jlo | 1, lastj = (jhi & 1) ? jhi : jhi - 1;
+        if (lastj >= first) total += (lastj - first) / 2 + 1;
+    }
+    return total;
+}
+
 uint64_t or_partitions(uint64_t n)
 {
     if (n < 4 || (n & 1)) return 0;

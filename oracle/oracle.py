@@ -77,6 +77,8 @@ def _load():
         lib.or_partitions.argtypes = [u64]
         lib.or_td_partitions.restype = u64
         lib.or_td_partitions.argtypes = [u64]
+        lib.or_count_strikes.restype = u64
+        lib.or_count_strikes.argtypes = [i64, u64, u64, u64]
         lib.or_prime_pi.restype = u64
         lib.or_prime_pi.argtypes = [u64, ctypes.c_int]
         _lib = lib
@@ -167,3 +169,9 @@ def td_partitions(n: int) -> int:
 
 def prime_pi(x: int, threads: int | None = None) -> int:
     return int(_load().or_prime_pi(x, threads or default_threads()))
+
+
+def count_strikes(a_odd: int, nbits: int, p_lo: int, p_hi: int) -> int:
+    """Strikes of the primes in [p_lo, p_hi] (from p^2 on) in the window of
+    nbits odd numbers from a_odd."""
+    return int(_load().or_count_strikes(a_odd, nbits, p_lo, p_hi))

@@ -62,3 +62,23 @@ def test_bucket_window_vs_oracle_full(gbm, monkeypatch, oracle):
     np.testing.assert_array_equal(bits[:nbits], ref)
     assert not bits[nbits:].any()
     assert pc == int(ref.sum())
+
+
+@pytest.mark.parametrize("A,nbits,mode", [
+    (10**9 + 1, 3 * (1 << 18) + 128, "atomic"),          # tile primes only
+    (10**12 - 999, (1 << 22) + 64, "atomic"),            # tile + slice primes (below 2^20)
+    (4 * 10**18 - 10**11 + 1, (1 << 26) + 64, "atomic"),  # tile + slice + atomic large primes
+    (4 * 10**18 - 10**11 + 1, (1 << 26) + 64, "bucket"),  # ... with the bucket lists
+])
+def test_strike_counters_equal_the_oracle(gbm, monkeypatch, oracle, A, nbits, mode):
+    """The work the roofline divides by: the kernels' strike counters equal the
+    oracle's count of (prime, multiple >= p^2) pairs, primes 47..sqrt."""
+    import math
+    with _ctx(gbm, monkeypatch, mode) as g:
+        q = torch.zeros(((nbits + 63) // 64,), dtype=torch.int64, device="cuda")
+        gbm.gb_profile_enable(g.handle, True)
+        g.sieve_segment(A, nbits, q)
+        w = gbm.gb_profile_work(g.handle)
+        gbm.gb_profile_enable(g.handle, False)
+    last = A + 2 * (nbits - 1)
+    assert w["sieve_strikes"] + w["large_strikes"] == oracle.count_strikes(A, nbits, 47, math.isqrt(last))

@@ -227,3 +227,22 @@ def test_partitions_hand_values(oracle):
 def test_partitions_bruteforce(oracle):
     for n in range(4, 3000, 2):
         assert oracle.partitions(n) == oracle.td_partitions(n), n
+
+
+@pytest.mark.parametrize("a,nbits,plo,phi", [
+    (1, 5000, 3, 10**6),
+    (10**6 + 1, 3001, 47, 10**6),
+    (10**9 + 7, 999, 5, 31),
+    (-41, 300, 3, 100),
+])
+def test_strike_count_brute_force(oracle, a, nbits, plo, phi):
+    # every odd number of the window, every prime in range: multiples >= p^2
+    last = a + 2 * (nbits - 1)
+    primes = [p for p in oracle.primes_upto(min(phi, math.isqrt(max(last, 0)))).tolist() if p >= plo and p > 2]
+    want = 0
+    for i in range(nbits):
+        m = a + 2 * i
+        if m < 4:
+            continue
+        want += sum(1 for p in primes if m % p == 0 and m >= p * p)
+    assert oracle.count_strikes(a, nbits, plo, phi) == want
