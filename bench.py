@@ -320,6 +320,21 @@ class PlainWork:
         return {"unresolved": int(r.unresolved), "max_pmin": int(r.max_pmin),
                 "max_pmin_n": int(r.max_pmin_n), "n_checked": int(r.n_checked)}
 
+    def algorithmic_cover_iterations(self):
+        """The cover's algorithmic work for one step (untimed): the generic
+        cover (cover_prefix 1) counts, per 64-n word, the odd primes applied
+        until the word is full -- equal to the oracle's count from the p_min
+        values (tests/test_gpu_work.py)."""
+        gb = self.gb
+        saved = self.ctx.config()["cover_prefix"]
+        self.ctx.set_config(cover_prefix=1)
+        gb.gb_profile_enable(self.ctx.handle, True)
+        self.step_device()
+        iters = gb.gb_profile_work(self.ctx.handle)["cover_iterations"]
+        gb.gb_profile_enable(self.ctx.handle, False)
+        self.ctx.set_config(cover_prefix=saved)
+        return iters
+
     def extra(self, args):
         if self.tuned is None:
             return {}
@@ -530,6 +545,8 @@ def main():
     for _ in range(args.warmup):
         work.step_device()
     torch.cuda.synchronize()
+    alg_cover = work.algorithmic_cover_iterations() if isinstance(work, PlainWork) else None
+    torch.cuda.synchronize()
 
     # ---- device-timed region (value), per-kernel events, clocks
     clocks = ClockSampler(local)
@@ -589,10 +606,16 @@ def main():
             # rotated mask) issued as a global atomic AND
             units = wk["large_strikes"] / nl
             ops = 2.0 * units
+        elif kern == "cover" and alg_cover is not None:
+            # algorithmic work: per 64-n word, the odd primes applied until
+            # the word is full (counted by the generic cover, equal to the
+            # oracle's count); 4 ALU ops each: the 64-bit funnel shift that
+            # aligns the partner bits (2) and the OR into C (2)
+            units = float(alg_cover)
+            ops = 4.0 * units
         elif kern == "cover":
-            # minimal ALU work: 2 ops per (32-bit coverage word, prime) step,
-            # the funnel shift that aligns the partner bits and the OR into C;
-            # 2 per probed (n, prime): shift and bit test
+            # (batched mode) the block cover's own steps: 2 ops per (32-bit
+            # coverage word, prime) step, 2 per probed (n, prime)
             units = wk["cover_iterations"] / nl
             ops = 2.0 * units
         else:
@@ -613,8 +636,9 @@ def main():
                 "unit": "T ALU lane-ops/s", "frac": per[kern]["frac"],
                 "traffic": per[kern]["dram_bytes_per_launch"],
                 "peak_source": "derived: 152 SMs x 64 ALU lanes x %.0f MHz (%s max clock)" % (sm_max, peak_src),
-                "work": ("cover: 2 ALU ops per (coverage word, prime) step and per probe; "
-                         "sieve: 2 per strike + 6 per stamped word"),
+                "work": ("cover: 4 ALU ops per (64-n word, odd prime) iteration until the word is full "
+                         "(algorithmic count); sieve: 2 per strike + 6 per stamped 32-bit word; "
+                         "large primes: 2 per strike"),
                 "kernels": per,
                 "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
 

@@ -74,7 +74,11 @@ typedef struct gb_config {
     uint32_t cover_prefix;  /* primes of the cover's unrolled phase (blocks of
                                64 over every word, then per-n probing): 64,
                                128, 192 or 256; 0 = chosen by the magnitude
-                               of n.  Outputs do not depend on it. */
+                               of n; 1 = the generic cover (one 64-n word per
+                               lane, primes looped until the word is full),
+                               whose work counter is the algorithmic count.
+                               Outputs do not depend on it (the batched mode
+                               treats 1 as 0). */
     uint64_t slab_bits;     /* most q-bits sieved and kept resident at once
                                (a slab is a run of whole segments); 0 = 2^33 */
     void*    stream;        /* cudaStream_t for all work; NULL = the legacy

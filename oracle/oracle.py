@@ -175,3 +175,21 @@ def count_strikes(a_odd: int, nbits: int, p_lo: int, p_hi: int) -> int:
     """Strikes of the primes in [p_lo, p_hi] (from p^2 on) in the window of
     nbits odd numbers from a_odd."""
     return int(_load().or_count_strikes(a_odd, nbits, p_lo, p_hi))
+
+
+def cover_iterations(lo: int, hi: int, P: int) -> int:
+    """Work of a loop-inverted cover over [lo, hi) (Sec. 2.3.1, the cover's
+    outer loop over primes): the sum over the 64-n words (word w holds
+    n = lo + 2 (64 w .. 64 w + 63)) of the number of odd primes applied in
+    ascending order until the word is full -- the largest position, among the
+    odd primes 3, 5, 7, ..., of p_min(n) over the word's n; 0 for n = 4
+    (p_min 2) and for n past hi; the count of odd primes <= P for an n with no
+    p <= P."""
+    pm = pmin_range(lo, hi, P).astype(np.int64)
+    primes = primes_upto(P).astype(np.int64)
+    K = len(primes) - 1
+    pos = np.searchsorted(primes, pm)             # 2 -> 0, 3 -> 1, 5 -> 2, ...
+    pos[pm == 0] = K
+    pad = (-len(pos)) % 64
+    pos = np.concatenate([pos, np.zeros(pad, dtype=np.int64)])
+    return int(pos.reshape(-1, 64).max(axis=1).sum())

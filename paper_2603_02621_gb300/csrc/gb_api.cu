@@ -291,9 +291,9 @@ int fill_defaults(gb_config& c)
     if (c.base_limit > (1ull << 32)) return fail(GB_EINVAL, "base_limit must be <= 2^32");
     if (c.p1 < 2 || c.p1 > (1u << 24) || c.p2 > (1u << 24))
         return fail(GB_EINVAL, "p1 must be in [2, 2^24] and p2 <= 2^24");
-    if (c.cover_prefix != 0 && c.cover_prefix != 64 && c.cover_prefix != 128 && c.cover_prefix != 192 &&
-        c.cover_prefix != 256)
-        return fail(GB_EINVAL, "cover_prefix must be 0, 64, 128, 192 or 256");
+    if (c.cover_prefix != 0 && c.cover_prefix != 1 && c.cover_prefix != 64 && c.cover_prefix != 128 &&
+        c.cover_prefix != 192 && c.cover_prefix != 256)
+        return fail(GB_EINVAL, "cover_prefix must be 0, 1, 64, 128, 192 or 256");
     if (c.slab_bits < c.seg_len) c.slab_bits = c.seg_len;
     return GB_OK;
 }
@@ -828,8 +828,8 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
         ca.iters = ctx->work_ptr(1);
         // two-phase kernel unless a p_min array is wanted (the generic kernel
         // writes it) or the pass has too few primes for its first phase
-        int KA = (pm || ctx->generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
-        if (KA && cfg.cover_prefix && cfg.cover_prefix <= K1) KA = (int)cfg.cover_prefix;
+        int KA = (pm || ctx->generic_cover || cfg.cover_prefix == 1) ? 0 : gb::cover_fast_phase_primes(K1, A0 + 2 * n_count);
+        if (KA && cfg.cover_prefix > 1 && cfg.cover_prefix <= K1) KA = (int)cfg.cover_prefix;
         if (KA) {
             // block cover: 7680 32-bit words per CTA (ten rounds of 96 words per
             // warp, the most its 10-bit counters allow)
@@ -1146,7 +1146,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
 
     // block-cover length (unrolled primes) for the batch's largest n
     int KA = ctx->generic_cover ? 0 : gb::cover_fast_phase_primes(K1, hi_max);
-    if (KA && cfg.cover_prefix && cfg.cover_prefix <= K1) KA = (int)cfg.cover_prefix;
+    if (KA && cfg.cover_prefix > 1 && cfg.cover_prefix <= K1) KA = (int)cfg.cover_prefix;
     if (!KA) return fail(GB_EINVAL, "gb_verify_batch needs P >= the 64th odd prime (313)");
 
     // the kernels of the batch, captured as one CUDA graph (re-used by update

@@ -177,8 +177,8 @@ extern "C" int gb_verify_range_noalloc(gb_ctx* ctx, uint64_t lo, uint64_t hi, ui
     ca.retry_count = counters;
     ca.retry_cap = (uint32_t)n_words;
     ca.has_n4 = (lo == 4);
-    int KA = (out->pmin || v.generic_cover) ? 0 : gb::cover_fast_phase_primes(K1, hi);
-    if (KA && v.ka_override && (uint32_t)v.ka_override <= K1) KA = v.ka_override;
+    int KA = (out->pmin || v.generic_cover || v.ka_override == 1) ? 0 : gb::cover_fast_phase_primes(K1, hi);
+    if (KA && v.ka_override > 1 && (uint32_t)v.ka_override <= K1) KA = v.ka_override;
     if (KA) {
         ca.cta_words = (uint32_t)std::min<uint64_t>(3840, S / 64);
         ca.chunks_per_seg = (uint32_t)((S / 64 + ca.cta_words - 1) / ca.cta_words);

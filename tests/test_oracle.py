@@ -246,3 +246,17 @@ def test_strike_count_brute_force(oracle, a, nbits, plo, phi):
             continue
         want += sum(1 for p in primes if m % p == 0 and m >= p * p)
     assert oracle.count_strikes(a, nbits, plo, phi) == want
+
+
+def test_cover_iterations_worked_by_hand(oracle):
+    # one 64-n word, n = 4 .. 130: the largest p_min there is 19 (at n = 98
+    # and n = 128: n - 3, ..., n - 17 are all composite, n - 19 is prime),
+    # the 7th odd prime; with P = 13 those n stay open and the word costs all
+    # 5 odd primes <= 13
+    assert oracle.pmin_single(98, 100) == 19 and oracle.pmin_single(128, 100) == 19
+    assert oracle.cover_iterations(4, 132, 1 << 10) == 7
+    assert oracle.cover_iterations(4, 132, 13) == 5
+    # words are independent: two words cost the sum of each alone
+    assert oracle.cover_iterations(4, 260, 1 << 10) == 7 + oracle.cover_iterations(132, 260, 1 << 10)
+    # a range of one n = 4 costs nothing
+    assert oracle.cover_iterations(4, 6, 1 << 10) == 0
