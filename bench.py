@@ -611,7 +611,7 @@ def main():
             # the word is full (counted by the generic cover, equal to the
             # oracle's count); 4 ALU ops each: the 64-bit funnel shift that
             # aligns the partner bits (2) and the OR into C (2)
-            units = float(alg_cover)
+            units = float(alg_cover) * args.steps / nl       # alg_cover is per step
             ops = 4.0 * units
         elif kern == "cover":
             # (batched mode) the block cover's own steps: 2 ops per (32-bit
