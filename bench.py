@@ -509,8 +509,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="plain", choices=sorted(PLAIN_MODES) + ["batched", "serving"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the timed stream")
-    ap.add_argument("--lanes", type=int, default=4, help="serving: server lanes")
-    ap.add_argument("--hbm-budget", type=int, default=64, help="serving: admission budget, GiB")
+    ap.add_argument("--lanes", type=int, default=2, help="serving: server lanes")
+    ap.add_argument("--hbm-budget", type=int, default=0, help="serving: admission budget, GiB (0: half the free HBM)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="plain family: run gb_autotune on the range first")
     ap.add_argument("--lo", type=int, default=None, help="custom range start (profiling of smaller cases)")

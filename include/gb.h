@@ -246,7 +246,8 @@ typedef struct gb_response {
     double t_done_us;           /* started, its batch finished */
 } gb_response;
 typedef struct gb_server gb_server;
-/* lanes 1..16; hbm_budget_bytes 0 = 8 GiB; max_batch 0 = 256 */
+/* lanes 1..16; hbm_budget_bytes 0 = half of the device memory free at
+ * creation (cudaMemGetInfo); max_batch 0 = 256 */
 int gb_server_create(gb_server** out, gb_ctx* ctx, uint32_t lanes, uint64_t hbm_budget_bytes, uint32_t max_batch);
 /* queue a request (GB_EINVAL if it is malformed or beyond base_limit^2) */
 int gb_server_submit(gb_server* srv, const gb_request* req, uint64_t* ticket);

@@ -172,7 +172,17 @@ extern "C" int gb_server_create(gb_server** out, gb_ctx* ctx, uint32_t lanes, ui
     if (rc) return rc;
     gb_server* s = new gb_server();
     s->parent = ctx;
-    s->budget = hbm_budget_bytes ? hbm_budget_bytes : (8ull << 30);
+    if (hbm_budget_bytes == 0) {
+        // admission by free device memory: half of what is free now
+        size_t free_b = 0, total_b = 0;
+        cudaSetDevice(cfg.device);
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            free_b = 16ull << 30;
+        }
+        hbm_budget_bytes = free_b / 2;
+    }
+    s->budget = hbm_budget_bytes;
     s->max_batch = max_batch ? max_batch : 256;
     s->base_limit = cfg.base_limit;
     cudaSetDevice(cfg.device);
