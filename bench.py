@@ -218,7 +218,7 @@ def cpu_baseline(mode: str = "plain", min_seconds: float = 12.0, seed: int = 11)
             used += len(batch)
     dt = time.perf_counter() - t0
     kind = {"batched": "ranges of the 4096-range batch", "serving": "range requests of the serving stream"}.get(
-        mode, "segments of " + mode)
+        mode, "segments of %d even n of [%d, %d)" % ((PLAIN_MODES[mode]["seg"],) + tuple(rank_range(mode, 0))))
     return {"value": done_n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{used} seeded {kind} ({done_n} n, {dt:.1f} s wall, P = 2^20)",
             "seconds": dt}
