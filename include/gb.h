@@ -85,6 +85,10 @@ typedef struct gb_config {
                                default stream */
 } gb_config;
 
+/* Largest hi of a range: the sieve window runs past hi by the halo (< 2^25)
+ * and must stay below 2^63. */
+#define GB_MAX_HI ((1ull << 63) - (1ull << 26))
+
 /* Per-segment output (Sec. 2.3.2): the segment holds the even n in [lo, hi). */
 typedef struct gb_segment_result {
     uint64_t lo, hi;

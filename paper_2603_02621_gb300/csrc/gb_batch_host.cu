@@ -27,7 +27,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     // per-range windows and work items
     uint64_t qwords = 0, n_sieve = 0, n_cover = 0, hi_max = 0, last_max = 0;
     for (uint32_t i = 0; i < count; ++i) {
-        if ((lo[i] & 1) || (hi[i] & 1) || lo[i] < 4 || hi[i] <= lo[i] || hi[i] > (1ull << 63))
+        if ((lo[i] & 1) || (hi[i] & 1) || lo[i] < 4 || hi[i] <= lo[i] || hi[i] > GB_MAX_HI)
             return fail(GB_EINVAL, "range must be even, lo >= 4, hi > lo");
         const uint64_t n = (hi[i] - lo[i]) / 2;
         if (n > (1ull << 32)) return fail(GB_EINVAL, "a batch range holds at most 2^32 even n");

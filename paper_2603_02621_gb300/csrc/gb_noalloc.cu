@@ -97,6 +97,7 @@ extern "C" int gb_verify_range_noalloc(gb_ctx* ctx, uint64_t lo, uint64_t hi, ui
 {
     if (!ctx || !out) return gb::set_error(GB_EINVAL, "NULL argument");
     if ((lo & 1) || (hi & 1) || lo < 4 || hi <= lo) return gb::set_error(GB_EINVAL, "range must be even, lo >= 4, hi > lo");
+    if (hi > GB_MAX_HI) return gb::set_error(GB_EINVAL, "hi beyond 2^63 - 2^26");
     gb::CtxView v{};
     int rc = gb::ctx_view(ctx, &v);
     if (rc) return rc;

@@ -72,7 +72,7 @@ int check_request(const gb_server* s, const gb_request& r)
 {
     if (r.kind == GB_REQ_QUERY) return ((r.lo & 1) || r.lo < 4 || r.lo >= (1ull << 63)) ? GB_EINVAL : GB_OK;
     if (r.kind != GB_REQ_RANGE) return GB_EINVAL;
-    if ((r.lo & 1) || (r.hi & 1) || r.lo < 4 || r.hi <= r.lo || r.hi > (1ull << 63)) return GB_EINVAL;
+    if ((r.lo & 1) || (r.hi & 1) || r.lo < 4 || r.hi <= r.lo || r.hi > GB_MAX_HI) return GB_EINVAL;
     if ((r.hi - r.lo) / 2 > (1ull << 32)) return GB_EINVAL;
     const double lim = (double)s->base_limit * (double)s->base_limit;
     if ((double)r.hi > lim) return GB_EINVAL;

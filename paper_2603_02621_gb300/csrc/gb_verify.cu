@@ -12,7 +12,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
 {
     if (!ctx || !out) return fail(GB_EINVAL, "NULL argument");
     if ((lo & 1) || (hi & 1) || lo < 4 || hi <= lo) return fail(GB_EINVAL, "range must be even, lo >= 4, hi > lo");
-    if (hi > (1ull << 63)) return fail(GB_EINVAL, "hi beyond 2^63");
+    if (hi > GB_MAX_HI) return fail(GB_EINVAL, "hi beyond 2^63 - 2^26");
     const gb_config& cfg = ctx->cfg;
     const uint32_t P1 = P ? P : cfg.p1;
     if (P1 < 2 || P1 > (1u << 24) || P1 > ctx->L) return fail(GB_EINVAL, "P out of range (2 .. min(2^24, base list))");

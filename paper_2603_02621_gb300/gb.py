@@ -19,6 +19,7 @@ import numpy as np
 from .build import LIB
 
 GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ETIMEOUT, GB_EBUSY, GB_ERANGE = range(7)
+GB_MAX_HI = (1 << 63) - (1 << 26)      # largest hi of a range (include/gb.h)
 
 
 class GbError(RuntimeError):

@@ -302,3 +302,24 @@ def test_invalid_ranges(ctx16, gbm):
         assert e.value.code == gbm.GB_EINVAL
     with pytest.raises(gbm.GbError):
         ctx16.verify_range(2**41, 2**41 + 10)     # sqrt beyond the 2^20 prime list
+
+
+def test_ranges_next_to_the_upper_limit(gbm, oracle):
+    """The last ranges the API takes (hi up to 2^63 - 2^26): records against
+    the oracle; one past the limit is refused."""
+    with gbm.Context(device=0, base_limit=1 << 32, seg_len=1 << 20, p1=1 << 15, p2=1 << 20) as g:
+        hi = gbm.GB_MAX_HI
+        lo = hi - 2 * 20000
+        r = g.verify_range(lo, hi)
+        # the oracle's Miller-Rabin p_min of every n (no window sieve to 3e9 needed)
+        pm = [oracle.pmin_single(n, 1 << 20) for n in range(lo, hi, 2)]
+        best = max(pm)
+        assert min(pm) > 0
+        assert [r["n_checked"], r["unresolved"], r["max_pmin"], r["max_pmin_n"]] == \
+            [len(pm), 0, best, lo + 2 * pm.index(best)]
+        b = g.verify_batch([(lo, hi)])["records"][0]
+        assert [b["max_pmin"], b["max_pmin_n"], b["unresolved"]] == [r["max_pmin"], r["max_pmin_n"], 0]
+        with pytest.raises(RuntimeError):
+            g.verify_range(hi, hi + 2)
+        with pytest.raises(RuntimeError):
+            g.verify_batch([(hi, hi + 2)])
