@@ -90,9 +90,12 @@ def workload_desc(mode: str, world: int):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi clocks, power and throttle reasons every 100 ms while running;
+    the SM clock is reported as the median over the samples taken under load
+    (GPU utilization >= 50 %), all samples if none was."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, device: int):
         self.device = device
@@ -103,7 +106,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except OSError:
@@ -120,22 +123,27 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-        sm, mx, reasons = [], 0.0, set()
+        sm, busy, mx, reasons = [], [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
+            if len(parts) < 8:
                 continue
             try:
-                sm.append(float(parts[0]))
+                clk = float(parts[0])
                 mx = max(mx, float(parts[1]))
+                util = float(parts[7])
             except ValueError:
                 continue
+            sm.append(clk)
+            if util >= 50.0:
+                busy.append(clk)
             for nm, v in zip(names, parts[3:7]):
                 if v.lower() == "active":
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        use = busy or sm
+        return {"sm_mhz": statistics.median(use) if use else None, "sm_max_mhz": mx or None,
+                "samples": len(sm), "samples_under_load": len(busy), "reasons": sorted(reasons)}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -542,19 +550,20 @@ def main():
             work.autotune(torch)
     ctx = work.ctx
 
+    alg_cover = work.algorithmic_cover_iterations() if isinstance(work, PlainWork) else None
+    torch.cuda.synchronize()
+    # clocks are sampled from the warm-up through the timed and end-to-end regions
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
     for _ in range(args.warmup):
         work.step_device()
     torch.cuda.synchronize()
-    alg_cover = work.algorithmic_cover_iterations() if isinstance(work, PlainWork) else None
-    torch.cuda.synchronize()
 
-    # ---- device-timed region (value), per-kernel events, clocks
-    clocks = ClockSampler(local)
+    # ---- device-timed region (value), per-kernel events
     gb.gb_profile_enable(ctx.handle, True)
     barrier(world, backend_ready)
     torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
