@@ -323,3 +323,26 @@ def test_ranges_next_to_the_upper_limit(gbm, oracle):
             g.verify_range(hi, hi + 2)
         with pytest.raises(RuntimeError):
             g.verify_batch([(hi, hi + 2)])
+
+
+def test_retry_list_overflow_is_redone(gbm):
+    """P1 = 31 leaves nearly every 64-n word of a 2^28-n slab open, more than
+    the retry list holds (2^21 words): the call is redone as one pass to P2
+    and must give the same totals as the ordinary P1 = 2^15 run."""
+    with gbm.Context(device=0, base_limit=1 << 20, seg_len=1 << 24, p1=1 << 15, p2=1 << 20) as g:
+        lo, hi = 10**9, 10**9 + 2 * (1 << 28)
+        ref = g.verify_range(lo, hi, hist_cap=4096)
+        got = g.verify_range(lo, hi, 31, hist_cap=4096)
+    for k in ("n_checked", "unresolved", "max_pmin", "max_pmin_n", "hist_len"):
+        assert got[k] == ref[k], k
+    np.testing.assert_array_equal(got["hist"], ref["hist"])
+    assert got["p_final"] == 1 << 20 and ref["unresolved"] == 0
+
+
+def test_histogram_capacity_too_small(ctx16, gbm, oracle):
+    lo, hi = 10**9, 10**9 + 2 * 40000
+    full = ctx16.verify_range(lo, hi, hist_cap=1024)
+    short = ctx16.verify_range(lo, hi, hist_cap=5, allow_erange=True)
+    assert short["rc"] == gbm.GB_ERANGE and full["rc"] == gbm.GB_OK
+    np.testing.assert_array_equal(short["hist"], full["hist"][:5])
+    assert short["max_pmin"] == full["max_pmin"] and short["hist_len"] == full["hist_len"] > 5
