@@ -6,7 +6,7 @@ Modes (--mode), each a workload of GoldbachGPU (arXiv 2603.02621):
   (Table 4's workload): one step = one gb_verify_range call: segment sieve of
   the q window, the loop-inverted cover with P1 = 2^15, the GPU retry pass to
   P2 = 2^20, per-segment reductions (Sec. 2.3);
-* exhaustive-1e12: [4, 10^12] (Table 5's range), segments of 2^27 even n,
+* exhaustive-1e12: [4, 10^12] (Table 4's largest range), segments of 2^27 even n,
   base primes to 2^31;
 * window-4e18: the 10^11-wide window [4e18 - 10^11, 4e18), segments of 2^27;
 * batched: 4096 ranges of uneven length (log-uniform 2^10..2^26 even n) and

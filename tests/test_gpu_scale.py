@@ -1,5 +1,5 @@
 """Exhaustive verification at scale (uint64 n): [4, 10^12] (the range of the
-paper's Table 5) and the 10^11-wide window below 4e18, segments of 2^27 even
+paper's Table 4) and the 10^11-wide window below 4e18, segments of 2^27 even
 n, base primes to 2^31, P1 = 2^15 then the retry pass to P2 = 2^20.
 
 Every segment's record and histogram row is checked against invariants and
