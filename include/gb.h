@@ -225,15 +225,19 @@ int gb_query(gb_ctx* ctx, uint64_t n, uint32_t* p_min);
 int gb_query_batch(gb_ctx* ctx, const uint64_t* n, uint32_t count, uint32_t P, uint32_t* p_min);
 
 /* ---------------------------------------------------------------- serving
- * A request loop with continuous batching.  The server owns `lanes` contexts
- * made from ctx by gb_init_shared (shared base primes, one stream each), each
- * driven by a host thread.  A free lane admits the requests at the head of
- * the FIFO queue that fit in the free part of the device-memory budget (at
- * most max_batch; a request larger than the whole budget runs alone) and runs
- * them as one gb_verify_batch call and one gb_query_batch call; requests that
- * arrive meanwhile are admitted by the next free lane, so their work overlaps
- * on the GPU.  Results do not depend on the batching.  ctx must outlive the
- * server and must not be used while the server runs. */
+ * A request loop with continuous batching.  The server owns lanes + 1
+ * contexts made from ctx by gb_init_shared (shared base primes, one stream
+ * each), each driven by a host thread.  Ranges enter a FIFO queue: a free
+ * range lane (lanes of them) admits the ranges at its head that fit in the
+ * free part of the device-memory budget (at most max_batch; a range larger
+ * than the whole budget runs alone) and runs them as one gb_verify_batch
+ * call; ranges that arrive meanwhile are admitted by the next free lane, so
+ * their work overlaps on the GPU.  Single-n queries enter a queue of their
+ * own, served by the extra lane on a stream of the highest priority: every
+ * queued query (at most max_batch) as one gb_query_batch call, so a query
+ * never waits behind ranges on the host.  Results do not depend on the
+ * batching.  ctx must outlive the server and must not be used while the
+ * server runs. */
 #define GB_REQ_RANGE 0   /* verify every even n in [lo, hi) (at most 2^32 n) */
 #define GB_REQ_QUERY 1   /* p_min(n) for n = lo */
 typedef struct gb_request {
@@ -250,7 +254,7 @@ typedef struct gb_response {
     double t_done_us;           /* started, its batch finished */
 } gb_response;
 typedef struct gb_server gb_server;
-/* lanes 1..16; hbm_budget_bytes 0 = half of the device memory free at
+/* lanes (range lanes) 1..16; hbm_budget_bytes 0 = half of the device memory free at
  * creation (cudaMemGetInfo); max_batch 0 = 256 */
 int gb_server_create(gb_server** out, gb_ctx* ctx, uint32_t lanes, uint64_t hbm_budget_bytes, uint32_t max_batch);
 /* queue a request (GB_EINVAL if it is malformed or beyond base_limit^2) */

@@ -2,15 +2,17 @@
 // several GPU lanes (GoldbachGPU, arXiv 2603.02621: range verification,
 // Sec. 2.3, and single-n checks, Sec. 2.4, served as a stream of requests).
 //
-// Requests (ranges to verify, single n to query) enter one FIFO queue.  Each
-// lane is a context sharing the base primes (gb_init_shared) with its own
-// stream and arenas, driven by its own host thread: whenever a lane is free it
-// admits the requests at the head of the queue, as many as fit in the free
-// part of the device-memory budget (at most max_batch), and runs them as one
-// gb_verify_batch call plus one gb_query_batch call.  Requests that arrive
-// while other lanes have work on the GPU are admitted by the next free lane,
-// so their work overlaps on the device.  A request's result does not depend
-// on what it was batched with.
+// Ranges to verify enter one FIFO queue, single-n queries another.  Each
+// range lane is a context sharing the base primes (gb_init_shared) with its
+// own stream and arenas, driven by its own host thread: whenever a lane is
+// free it admits the ranges at the head of the queue, as many as fit in the
+// free part of the device-memory budget (at most max_batch), and runs them as
+// one gb_verify_batch call.  Ranges that arrive while other lanes have work on
+// the GPU are admitted by the next free lane, so their work overlaps on the
+// device.  Queries take microseconds each and should not wait behind ranges:
+// one more lane, on a stream of the highest priority, serves only them, every
+// queued query as one gb_query_batch call.  A request's result does not
+// depend on what it was batched with.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -42,8 +44,9 @@ struct gb_server {
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Pending> queue;
+    std::condition_variable cv_work, cv_query, cv_done;
+    std::deque<Pending> queue;      // ranges
+    std::deque<Pending> qqueue;     // single-n queries
     std::unordered_map<uint64_t, gb_response> done;
     uint64_t next_ticket = 1;
     uint64_t in_flight = 0, in_flight_max = 0;
@@ -79,24 +82,47 @@ int check_request(const gb_server* s, const gb_request& r)
     return GB_OK;
 }
 
-void lane_loop(gb_server* s, size_t lane)
+void post(gb_server* s, const std::vector<gb_server::Pending>& batch, int rc, double t_start,
+          const std::vector<gb_segment_result>& recs, const std::vector<uint32_t>& pm)
+{
+    const double t_done = s->now_us();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (size_t i = 0; i < batch.size(); ++i) {
+            const gb_server::Pending& p = batch[i];
+            gb_response r{};
+            r.t_submit_us = p.t_submit;
+            r.t_start_us = t_start;
+            r.t_done_us = t_done;
+            r.status = rc;
+            if (p.req.kind == GB_REQ_RANGE) r.range = recs[i];
+            else r.p_min = pm[i];
+            s->done[p.ticket] = r;
+            s->in_flight -= p.bytes;
+        }
+        s->n_done += batch.size();
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+}
+
+// a range lane: admits ranges from the head of the queue within the budget
+void range_loop(gb_server* s, size_t lane)
 {
     gb_ctx* ctx = s->lanes[lane];
-    gb_config cfg{};
-    gb_get_config(ctx, &cfg);
     std::vector<gb_server::Pending> batch;
-    std::vector<uint64_t> lo, hi, qn;
+    std::vector<uint64_t> lo, hi;
     std::vector<gb_segment_result> recs;
-    std::vector<uint32_t> pm;
+    const std::vector<uint32_t> none;
     for (;;) {
-        uint64_t held = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
             if (s->queue.empty()) return;                           // stopping and drained
-            // admission: head of the queue while it fits the free budget (the
-            // first request always, if nothing else is in flight)
+            // the head of the queue while it fits the free budget (the first
+            // request always, if nothing else is in flight)
             batch.clear();
+            uint64_t held = 0;
             while (!s->queue.empty() && batch.size() < s->max_batch) {
                 const gb_server::Pending& p = s->queue.front();
                 const bool fits = s->in_flight + held + p.bytes <= s->budget;
@@ -118,44 +144,46 @@ void lane_loop(gb_server* s, size_t lane)
         const double t_start = s->now_us();
         lo.clear();
         hi.clear();
-        qn.clear();
         for (const auto& p : batch) {
-            if (p.req.kind == GB_REQ_RANGE) {
-                lo.push_back(p.req.lo);
-                hi.push_back(p.req.hi);
-            } else {
-                qn.push_back(p.req.lo);
-            }
+            lo.push_back(p.req.lo);
+            hi.push_back(p.req.hi);
         }
         recs.assign(lo.size(), gb_segment_result{});
-        pm.assign(qn.size(), 0u);
-        int rc_r = GB_OK, rc_q = GB_OK;
-        if (!lo.empty())
-            rc_r = gb_verify_batch(ctx, lo.data(), hi.data(), (uint32_t)lo.size(), 0, recs.data(), nullptr, 0);
-        if (!qn.empty()) rc_q = gb_query_batch(ctx, qn.data(), (uint32_t)qn.size(), 0, pm.data());
-        const double t_done = s->now_us();
+        const int rc = gb_verify_batch(ctx, lo.data(), hi.data(), (uint32_t)lo.size(), 0, recs.data(), nullptr, 0);
+        post(s, batch, rc, t_start, recs, none);
+    }
+}
+
+// the query lane: every queued query (at most max_batch) as one batch
+void query_loop(gb_server* s, size_t lane)
+{
+    gb_ctx* ctx = s->lanes[lane];
+    std::vector<gb_server::Pending> batch;
+    std::vector<uint64_t> qn;
+    std::vector<uint32_t> pm;
+    const std::vector<gb_segment_result> none;
+    for (;;) {
         {
-            std::lock_guard<std::mutex> lk(s->mu);
-            size_t ir = 0, iq = 0;
-            for (const auto& p : batch) {
-                gb_response r{};
-                r.t_submit_us = p.t_submit;
-                r.t_start_us = t_start;
-                r.t_done_us = t_done;
-                if (p.req.kind == GB_REQ_RANGE) {
-                    r.status = rc_r;
-                    r.range = recs[ir++];
-                } else {
-                    r.status = rc_q;
-                    r.p_min = pm[iq++];
-                }
-                s->done[p.ticket] = r;
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_query.wait(lk, [&] { return s->stop || !s->qqueue.empty(); });
+            if (s->qqueue.empty()) return;
+            batch.clear();
+            uint64_t held = 0;
+            while (!s->qqueue.empty() && batch.size() < s->max_batch) {
+                held += s->qqueue.front().bytes;
+                batch.push_back(s->qqueue.front());
+                s->qqueue.pop_front();
             }
-            s->in_flight -= held;
-            s->n_done += batch.size();
+            s->in_flight += held;
+            s->in_flight_max = std::max(s->in_flight_max, s->in_flight);
+            s->n_batches += 1;
         }
-        s->cv_done.notify_all();
-        s->cv_work.notify_all();
+        const double t_start = s->now_us();
+        qn.clear();
+        for (const auto& p : batch) qn.push_back(p.req.lo);
+        pm.assign(qn.size(), 0u);
+        const int rc = gb_query_batch(ctx, qn.data(), (uint32_t)qn.size(), 0, pm.data());
+        post(s, batch, rc, t_start, none, pm);
     }
 }
 
@@ -186,10 +214,18 @@ extern "C" int gb_server_create(gb_server** out, gb_ctx* ctx, uint32_t lanes, ui
     s->max_batch = max_batch ? max_batch : 256;
     s->base_limit = cfg.base_limit;
     cudaSetDevice(cfg.device);
-    for (uint32_t i = 0; i < lanes; ++i) {
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+        cudaGetLastError();
+        prio_lo = prio_hi = 0;
+    }
+    // lanes 0..lanes-1 verify ranges; lane `lanes` answers queries on a
+    // stream of the highest priority
+    for (uint32_t i = 0; i <= lanes; ++i) {
         cudaStream_t st = nullptr;
         gb_ctx* lc = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        const int prio = i == lanes ? prio_hi : prio_lo;
+        if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio) != cudaSuccess ||
             (rc = gb_init_shared(&lc, ctx, st)) != GB_OK) {
             if (st) cudaStreamDestroy(st);
             gb_server_destroy(s);
@@ -198,7 +234,8 @@ extern "C" int gb_server_create(gb_server** out, gb_ctx* ctx, uint32_t lanes, ui
         s->streams.push_back(st);
         s->lanes.push_back(lc);
     }
-    for (uint32_t i = 0; i < lanes; ++i) s->threads.emplace_back(lane_loop, s, (size_t)i);
+    for (uint32_t i = 0; i < lanes; ++i) s->threads.emplace_back(range_loop, s, (size_t)i);
+    s->threads.emplace_back(query_loop, s, (size_t)lanes);
     *out = s;
     return GB_OK;
 }
@@ -214,10 +251,12 @@ extern "C" int gb_server_submit(gb_server* s, const gb_request* req, uint64_t* t
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return GB_EBUSY;
         *ticket = s->next_ticket++;
-        s->queue.push_back({*ticket, *req, request_bytes(*req, std::max(cfg.p1, cfg.p2)), s->now_us()});
+        const gb_server::Pending p{*ticket, *req, request_bytes(*req, std::max(cfg.p1, cfg.p2)), s->now_us()};
+        (req->kind == GB_REQ_QUERY ? s->qqueue : s->queue).push_back(p);
         s->n_submitted += 1;
     }
-    s->cv_work.notify_one();
+    if (req->kind == GB_REQ_QUERY) s->cv_query.notify_one();
+    else s->cv_work.notify_one();
     return GB_OK;
 }
 
@@ -255,6 +294,7 @@ extern "C" void gb_server_destroy(gb_server* s)
         s->stop = true;
     }
     s->cv_work.notify_all();
+    s->cv_query.notify_all();
     s->cv_done.notify_all();
     for (auto& t : s->threads) t.join();
     for (gb_ctx* c : s->lanes) gb_destroy(c);

@@ -125,6 +125,22 @@ def test_serving_concurrent_submitters(gbm, sctx):
     assert len(res) == len(reqs) and all(r["status"] == 0 for r in res.values())
 
 
+def test_serving_queries_do_not_wait_for_ranges(gbm, sctx, oracle):
+    """Queries have a lane of their own: queued behind long ranges, they are
+    still answered before those ranges finish."""
+    with gbm.Server(sctx, lanes=1, hbm_budget=8 << 30, max_batch=64) as srv:
+        big = [srv.submit("range", 10**15 + 2**34 * i, 10**15 + 2**34 * i + 2**33) for i in range(4)]
+        qn = [10**18 + 2 * k for k in range(1, 33)]
+        qt = [srv.submit("query", n) for n in qn]
+        qr = [srv.wait(t) for t in qt]
+        rr = [srv.wait(t) for t in big]
+    assert all(r["status"] == 0 for r in qr + rr)
+    assert all(r["range"]["unresolved"] == 0 for r in rr)
+    assert max(r["t_done_us"] for r in qr) < max(r["t_done_us"] for r in rr)
+    for n, r in zip(qn, qr):
+        assert r["p_min"] == oracle.pmin_single(n, P2)
+
+
 def test_shared_context_lifetime(gbm, oracle):
     """Contexts made by gb_init_shared use the parent's base primes; the
     primes stay valid until the last context holding them is destroyed,
