@@ -71,9 +71,11 @@ typedef struct gb_config {
     uint32_t p1;            /* first-pass bound P1 (p <= P1); 0 = 2^15 */
     uint32_t p2;            /* retry-pass bound P2; 0 or <= p1 = no retry pass;
                                <= 2^24 */
-    uint32_t cover_prefix;  /* primes of the cover's unrolled phase (blocks of
-                               64 over every word, then per-n probing): 64,
-                               128, 192 or 256; 0 = chosen by the magnitude
+    uint32_t cover_prefix;  /* primes of the cover's unrolled phase, a
+                               multiple of 16 in [48, 256]: a first block of
+                               48 (prefix = 16 mod 32) or 64 primes over every
+                               word, blocks of 32 over the words still open,
+                               then per-n probing; 0 = chosen by the magnitude
                                of n; 1 = the generic cover (one 64-n word per
                                lane, primes looped until the word is full),
                                whose work counter is the algorithmic count.

@@ -40,9 +40,8 @@ int fill_defaults(gb_config& c)
     if (c.base_limit > (1ull << 32)) return fail(GB_EINVAL, "base_limit must be <= 2^32");
     if (c.p1 < 2 || c.p1 > (1u << 24) || c.p2 > (1u << 24))
         return fail(GB_EINVAL, "p1 must be in [2, 2^24] and p2 <= 2^24");
-    if (c.cover_prefix != 0 && c.cover_prefix != 1 && c.cover_prefix != 64 && c.cover_prefix != 128 &&
-        c.cover_prefix != 192 && c.cover_prefix != 256)
-        return fail(GB_EINVAL, "cover_prefix must be 0, 1, 64, 128, 192 or 256");
+    if (c.cover_prefix > 1 && !gb::cover_prefix_valid((int)c.cover_prefix))
+        return fail(GB_EINVAL, "cover_prefix must be 0, 1 or a multiple of 16 in [48, 256]");
     if (c.slab_bits < c.seg_len) c.slab_bits = c.seg_len;
     return GB_OK;
 }
@@ -343,7 +342,7 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     }
     if (const char* e = getenv("GB_KA")) {
         const int v = atoi(e);
-        if ((v == 64 || v == 128 || v == 192 || v == 256) && ctx->cfg.cover_prefix == 0) ctx->cfg.cover_prefix = v;
+        if (gb::cover_prefix_valid(v) && ctx->cfg.cover_prefix == 0) ctx->cfg.cover_prefix = v;
     }
     rc = build_primes(ctx);
     if (rc) {

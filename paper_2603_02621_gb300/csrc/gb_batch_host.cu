@@ -176,7 +176,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     // block-cover length (unrolled primes) for the batch's largest n
     int KA = ctx->generic_cover ? 0 : gb::cover_fast_phase_primes(K1, hi_max);
     if (KA && cfg.cover_prefix > 1 && cfg.cover_prefix <= K1) KA = (int)cfg.cover_prefix;
-    if (!KA) return fail(GB_EINVAL, "gb_verify_batch needs P >= the 64th odd prime (313)");
+    if (!KA) return fail(GB_EINVAL, "gb_verify_batch needs P >= the 48th odd prime (227)");
 
     // the kernels of the batch, captured as one CUDA graph (re-used by update
     // while the sequence keeps its shape) or launched one by one

@@ -147,14 +147,19 @@ struct CoverArgs {
     // segments whose key in maxkey_check is still 0 and writes it to maxkey
     int max_only;
     const unsigned long long* maxkey_check;
+    // block cover only (set by the launcher): blocks of 32 primes after block 0
+    uint32_t n_later;
+    uint32_t cum_wt[3];         // 1, 2^10, 2^20: weights of the packed 10-bit counters
 };
 cudaError_t launch_cover(const CoverArgs& a, int threads, cudaStream_t s);
 
-// Block cover (k_cover_fast): unrolled blocks of 64 primes, the first over
-// every 32-bit coverage word, each later one over the words still open; then,
-// in the same kernel, each n still open probes the primes KA+1 .. K in order
-// (KA = 64 x blocks).  Needs K >= KA, H = 4 (mod 64) and no p_min array.
+// Block cover (k_cover_fast): unrolled blocks, the first (48 or 64 primes)
+// over every 32-bit coverage word, each later one (32 primes) over the words
+// still open; then, in the same kernel, each n still open probes the primes
+// KA+1 .. K in order (KA = 48 or 64 + 32 x later blocks, at most 256; 48 when
+// KA = 16 mod 32).  Needs K >= KA, H = 4 (mod 64) and no p_min array.
 int cover_fast_phase_primes(uint32_t K, uint64_t n_hi);   // KA for K primes near n_hi (0: none)
+bool cover_prefix_valid(int KA);
 cudaError_t launch_cover_fast(const CoverArgs& a, int KA, cudaStream_t s);
 
 // Sieve and block cover fused per CTA (k_seg_cover): the window is sieved

@@ -129,7 +129,7 @@ extern "C" int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, 
                           c.p1 = v;
                           return true;
                       }});
-    params.push_back({{64, 128, 192, 256}, [](gb_config& c, uint32_t v) {
+    params.push_back({{80, 112, 144, 176, 208, 240}, [](gb_config& c, uint32_t v) {
                           c.cover_prefix = v;
                           return true;
                       }});

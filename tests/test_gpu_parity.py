@@ -199,14 +199,15 @@ def test_two_phase_without_retry_counts_unresolved(gbm, oracle):
     assert r["max_pmin"] == int(ref.max())
 
 
-@pytest.mark.parametrize("ka", ["64", "128", "192", "256"])
-@pytest.mark.parametrize("lo", [10**6, 3 * 10**11])
+@pytest.mark.parametrize("ka", ["48", "64", "80", "144", "192", "256"])
+@pytest.mark.parametrize("lo", [10**6, 3 * 10**11, 4 * 10**18 - 10**7])
 def test_two_phase_matches_generic(gbm, monkeypatch, ka, lo):
-    """The block cover (1 to 4 unrolled blocks of 64 primes, so the segment
-    maximum comes from the probing or from a re-run of the last block) and the
+    """The block cover (a first block of 48 or 64 primes and 0 to 6 blocks of
+    32, so the segment maximum comes from the probing or from a re-run of the
+    last block that set a bit, with its input list kept or overwritten) and the
     generic cover kernel give identical results."""
     hi = lo + 2 * 5 * 10**6
-    base = dict(device=0, base_limit=1 << 20, seg_len=1 << 20, p1=1 << 15, p2=1 << 20)
+    base = dict(device=0, base_limit=1 << 31, seg_len=1 << 20, p1=1 << 15, p2=1 << 20)
     monkeypatch.setenv("GB_KA", ka)
     with gbm.Context(**base) as g:
         a = g.verify_range(lo, hi, seg_hist_stride=3512, hist_cap=3512)
@@ -214,6 +215,29 @@ def test_two_phase_matches_generic(gbm, monkeypatch, ka, lo):
     monkeypatch.setenv("GB_COVER", "generic")
     with gbm.Context(**base) as g:
         b = g.verify_range(lo, hi, seg_hist_stride=3512, hist_cap=3512)
+    assert a["segs"] == b["segs"]
+    assert np.array_equal(a["seg_hist"], b["seg_hist"])
+
+
+@pytest.mark.parametrize("p1,ka", [(420, "80"), (227, "48"), (313, "64"), (617, "112")])
+def test_block_cover_maximum_without_probing(gbm, monkeypatch, p1, ka):
+    """P1 holds exactly as many odd primes as the blocks (K = KA: 80 up to
+    420, 48 up to 227, 64 up to 313, 112 up to 617), so no n is settled by
+    probing and every
+    warp takes its maximum from a re-run: near 4e18 block 0 leaves most words
+    open, so the later block writes over its input and the re-run goes
+    through every block; without a retry pass the open n count as
+    unresolved.  Identical to the generic cover."""
+    lo, hi = 4 * 10**18 - 2 * 3 * 10**6, 4 * 10**18
+    base = dict(device=0, base_limit=1 << 31, seg_len=1 << 20, p1=p1, p2=0)
+    monkeypatch.setenv("GB_KA", ka)
+    with gbm.Context(**base) as g:
+        a = g.verify_range(lo, hi, seg_hist_stride=128, hist_cap=128)
+    monkeypatch.delenv("GB_KA")
+    monkeypatch.setenv("GB_COVER", "generic")
+    with gbm.Context(**base) as g:
+        b = g.verify_range(lo, hi, seg_hist_stride=128, hist_cap=128)
+    assert a["unresolved"] > 0
     assert a["segs"] == b["segs"]
     assert np.array_equal(a["seg_hist"], b["seg_hist"])
 
