@@ -603,7 +603,7 @@ def main():
     # issue rate, measured by a shift/or loop) x the maximum SM clock.
     alu_peak = 152 * 64 * sm_max * 1e6 / 1e12            # T ALU lane-ops/s
     # DRAM bytes per unit measured by ncu on [4, 2^32] (plain workload's kernels)
-    ncu_traffic = {"cover": 0.1269, "sieve": 0.09657} if args.mode == "plain" else {}
+    ncu_traffic = {"cover": 0.1270, "sieve": 0.09678} if args.mode == "plain" else {}
     per = {}
     for kern in ("sieve", "cover", "large"):
         kp = prof[kern]
