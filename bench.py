@@ -91,9 +91,12 @@ def workload_desc(mode: str, world: int):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks, power and throttle reasons every 100 ms while running;
-    the SM clock is reported as the median over the samples taken under load
-    (GPU utilization >= 50 %), all samples if none was."""
+    """nvidia-smi clocks, power and throttle reasons every 20 ms while running,
+    each sample stamped on arrival.  The SM clock and the throttle reasons are
+    taken over the samples that arrived inside the timed regions (between
+    mark_start and mark_end, plus 50 ms for the output to arrive); if a region
+    was too short to catch one, over the samples taken under load (GPU
+    utilization >= 50 %), else over all samples."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap,utilization.gpu")
@@ -102,20 +105,28 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.lines = []
+        self.t_start = None
+        self.t_end = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except OSError:
             self.proc = None
 
+    def mark_start(self):
+        self.t_start = time.monotonic()
+
+    def mark_end(self):
+        self.t_end = time.monotonic()
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
     def stop(self):
         if self.proc:
@@ -124,9 +135,9 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-        sm, busy, mx, reasons = [], [], 0.0, set()
+        rows, mx = [], 0.0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in list(self.lines):
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -136,15 +147,16 @@ class ClockSampler:
                 util = float(parts[7])
             except ValueError:
                 continue
-            sm.append(clk)
-            if util >= 50.0:
-                busy.append(clk)
-            for nm, v in zip(names, parts[3:7]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        use = busy or sm
-        return {"sm_mhz": statistics.median(use) if use else None, "sm_max_mhz": mx or None,
-                "samples": len(sm), "samples_under_load": len(busy), "reasons": sorted(reasons)}
+            rows.append((t, clk, util, {nm for nm, v in zip(names, parts[3:7]) if v.lower() == "active"}))
+        inside = []
+        if self.t_start is not None and self.t_end is not None:
+            inside = [r for r in rows if self.t_start <= r[0] <= self.t_end + 0.05]
+        busy = [r for r in rows if r[2] >= 50.0]
+        use = inside or busy or rows
+        reasons = set().union(*(r[3] for r in use)) if use else set()
+        return {"sm_mhz": statistics.median(r[1] for r in use) if use else None, "sm_max_mhz": mx or None,
+                "samples": len(rows), "samples_in_timed_region": len(inside), "samples_under_load": len(busy),
+                "reasons": sorted(reasons)}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -466,7 +478,10 @@ def run_serving(args, gb, torch, world, rank, local, backend_ready):
     clocks = ClockSampler(local)
     barrier(world, backend_ready)
     clocks.start()
+    time.sleep(0.1)
+    clocks.mark_start()
     out, wall, st = serve(reqs, args.lanes)
+    clocks.mark_end()
     clk = clocks.stop()
     barrier(world, backend_ready)
     bad = [r for r in out if r["status"] != 0]
@@ -566,6 +581,7 @@ def main():
     barrier(world, backend_ready)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark_start()
     ev0.record(stream)
     for _ in range(args.steps):
         work.step_device()
@@ -587,6 +603,7 @@ def main():
         work.step_host()
     torch.cuda.synchronize()
     e2e_ms = 1000.0 * (time.perf_counter() - t0)
+    clocks.mark_end()
     clk = clocks.stop()
     e2e_ms = reduce_max(e2e_ms, world, backend_ready)
 

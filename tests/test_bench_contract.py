@@ -37,3 +37,24 @@ def test_reference_arm_rank_nonzero_is_silent():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                           "--warmup", "0"], capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
     assert out.returncode == 0 and not [l for l in out.stdout.splitlines() if l.startswith("{")]
+
+
+def test_clock_sampler_takes_the_timed_window():
+    """Clock samples are stamped on arrival; the reported SM clock and the
+    throttle reasons come from the samples inside the marked timed region,
+    and from the samples under load when the region caught none."""
+    sys.path.insert(0, ROOT)
+    import bench
+    row = "{clk}, 2070, 900.0, Not Active, Not Active, Not Active, {cap}, {util}"
+    c = bench.ClockSampler(0)
+    c.lines = [(1.0, row.format(clk=1200, cap="Not Active", util=0)),
+               (2.0, row.format(clk=2070, cap="Active", util=100)),
+               (2.1, row.format(clk=2040, cap="Not Active", util=100)),
+               (3.0, row.format(clk=1500, cap="Not Active", util=90))]
+    c.t_start, c.t_end = 1.95, 2.06
+    r = c.stop()
+    assert r["samples"] == 4 and r["samples_in_timed_region"] == 2 and r["samples_under_load"] == 3
+    assert r["sm_mhz"] == (2070 + 2040) / 2 and r["sm_max_mhz"] == 2070 and r["reasons"] == ["sw_power_cap"]
+    c.t_start, c.t_end = 2.5, 2.6                       # a region too short to catch a sample
+    r = c.stop()
+    assert r["samples_in_timed_region"] == 0 and r["sm_mhz"] == 2040
