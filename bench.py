@@ -241,6 +241,7 @@ def cpu_baseline(mode: str = "plain", min_seconds: float = 12.0, seed: int = 11)
     kind = {"batched": "ranges of the 4096-range batch", "serving": "range requests of the serving stream"}.get(
         mode, "segments of %d even n of [%d, %d)" % ((PLAIN_MODES[mode]["seg"],) + tuple(rank_range(mode, 0))))
     return {"value": done_n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "value_per_core": done_n / dt / threads,
             "sample": f"{used} seeded {kind} ({done_n} n, {dt:.1f} s wall, P = 2^20)",
             "seconds": dt}
 
@@ -265,7 +266,7 @@ def run_reference(args, world, rank):
             "vs_baseline": value / PAPER_BY_MODE[args.mode] if args.mode in PAPER_BY_MODE else None,
             "dtype": "u64", "data": "synthetic", "mode": args.mode, "config": workload_desc(args.mode, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+                             "value_per_core": value / last["cores"], "sample": last["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
