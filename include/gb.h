@@ -65,9 +65,13 @@ typedef struct gb_config {
     uint32_t cta_threads;   /* threads per segment-sieve CTA: 128, 256 or
                                512; 0 = 256 */
     uint32_t bucket_split;  /* sieving primes >= this are struck by the
-                               large-prime pass (one start per L2-sized chunk
-                               of the window, global atomic AND) instead of
-                               per tile in shared memory; 0 = tile_bits */
+                               large-prime passes (per 2^20-bit shared-memory
+                               slice below 2^20, else one start per L2-sized
+                               chunk of the window, global atomic AND)
+                               instead of per tile in shared memory; 0 = by
+                               magnitude: 2^16 (at most tile_bits) when the
+                               window's sieving primes reach 2^18, else
+                               tile_bits */
     uint32_t p1;            /* first-pass bound P1 (p <= P1); 0 = 2^15 */
     uint32_t p2;            /* retry-pass bound P2; 0 or <= p1 = no retry pass;
                                <= 2^24 */

@@ -28,7 +28,6 @@ int fill_defaults(gb_config& c)
     if (c.base_limit == 0) c.base_limit = 1u << 16;
     if (c.tile_bits == 0) c.tile_bits = 1u << 18;
     if (c.cta_threads == 0) c.cta_threads = 256;
-    if (c.bucket_split == 0) c.bucket_split = c.tile_bits;
     if (c.p1 == 0) c.p1 = 1u << 15;
     if (c.slab_bits == 0) c.slab_bits = 1ull << 33;
     if (c.seg_len % 2048 || c.seg_len > (1u << 30))
@@ -56,7 +55,7 @@ int tile_sieve_args(gb_ctx* ctx, int64_t B, uint64_t nbits, gb::SieveArgs& a, ui
     const uint64_t r = last > 0 ? isqrt_u64((uint64_t)last) : 0;
     if (r > ctx->L) return fail(GB_EINVAL, "window beyond base_limit^2");
     np = ctx->pi(r);                                // primes <= sqrt(last)
-    nsmall = std::min<uint64_t>(np, std::max<uint64_t>(ctx->pi(ctx->cfg.bucket_split - 1), gb::kFirstStrikeIdx));
+    nsmall = std::min<uint64_t>(np, std::max<uint64_t>(ctx->pi(ctx->split(r) - 1), gb::kFirstStrikeIdx));
     a = gb::SieveArgs{};
     a.B = B;
     a.nbits = nbits;
@@ -101,7 +100,8 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
         la.strikes = ctx->work_ptr(2);
         // primes below mid_limit: per 2^20-bit slice in shared memory
         uint64_t nmid = nsmall;
-        if (ctx->mid_limit > ctx->cfg.bucket_split) {
+        const int64_t last = B + 2 * (int64_t)(nbits - 1);
+        if (ctx->mid_limit > ctx->split(isqrt_u64((uint64_t)last))) {
             nmid = std::min<uint64_t>(np, std::max<uint64_t>(nsmall, ctx->pi(ctx->mid_limit - 1)));
             if (nmid > nsmall) {
                 gb::LargeArgs ma = la;
@@ -453,7 +453,7 @@ int gb_prime_pi(gb_ctx* ctx, uint64_t x, uint64_t* count)
     const uint64_t total = (x - 1) / 2;             // odd numbers 3 .. x
     const uint64_t chunk = ctx->cfg.slab_bits;
     // primes from bucket_split on strike into a buffer, so sieve into the slab buffer
-    const bool need_buf = ctx->pi(isqrt_u64(x)) > ctx->pi(ctx->cfg.bucket_split - 1);
+    const bool need_buf = ctx->pi(isqrt_u64(x)) > ctx->pi(ctx->split(isqrt_u64(x)) - 1);
     if (need_buf && (rc = ctx->q.ensure(((std::min(chunk, total) + 63) / 64) * 8))) return rc;
     for (uint64_t done = 0; done < total; done += chunk) {
         const uint64_t nb = std::min(chunk, total - done);

@@ -45,8 +45,9 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     // the split strike per tile, those below the mid limit per 2^20-bit slice
     // of each window in shared memory, the rest per window piece by atomics
     const uint64_t np = ctx->pi(isqrt_u64(last_max));
-    const uint64_t nsmall = std::min<uint64_t>(np, std::max<uint64_t>(ctx->pi(cfg.bucket_split - 1), gb::kFirstStrikeIdx));
-    const uint64_t nmid = ctx->mid_limit > cfg.bucket_split
+    const uint32_t split = ctx->split(isqrt_u64(last_max));
+    const uint64_t nsmall = std::min<uint64_t>(np, std::max<uint64_t>(ctx->pi(split - 1), gb::kFirstStrikeIdx));
+    const uint64_t nmid = ctx->mid_limit > split
                               ? std::min<uint64_t>(np, std::max<uint64_t>(nsmall, ctx->pi(ctx->mid_limit - 1)))
                               : nsmall;
     uint64_t n_mid = 0;

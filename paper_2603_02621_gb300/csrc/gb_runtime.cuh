@@ -253,6 +253,15 @@ struct gb_ctx {
     {
         return (uint64_t)(std::upper_bound(base->h_primes.begin(), base->h_primes.end(), (uint32_t)std::min<uint64_t>(x, 0xffffffffull)) - base->h_primes.begin());
     }
+    // tile / large-prime split for a window whose sieving primes reach r: the
+    // configured one, else by magnitude -- when primes reach 2^18 the ones
+    // above 2^16 hit a tile at most a few times and go faster to the
+    // shared-memory slices than through per-tile starts
+    uint32_t split(uint64_t r) const
+    {
+        if (cfg.bucket_split) return cfg.bucket_split;
+        return r >= (1u << 18) ? std::min<uint32_t>(1u << 16, cfg.tile_bits) : cfg.tile_bits;
+    }
 };
 
 // context configuration defaults and checks (gb_init, gb_set_config)
