@@ -111,7 +111,7 @@ def test_batch_rejects_bad_input(ctx, gbm):
     with pytest.raises(RuntimeError):
         ctx.verify_batch([(10**6, 10**6)])
     with pytest.raises(RuntimeError):
-        ctx.verify_batch([(10**6, 10**6 + 100)], 17)     # fewer than 64 odd primes
+        ctx.verify_batch([(10**6, 10**6 + 100)], 17)     # fewer than 48 odd primes
     out = ctx.verify_batch([(10**9, 10**9 + 2 * 5000)], hist_stride=3, allow_erange=True)
     assert out["rc"] == gbm.GB_ERANGE and out["records"][0]["hist_len"] > 3
 
