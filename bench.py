@@ -246,6 +246,72 @@ def cpu_baseline(mode: str = "plain", min_seconds: float = 12.0, seed: int = 11)
             "seconds": dt}
 
 
+def roofline_of(prof, wk, alg_cover, steps, mode, peaks, peak_src):
+    """Roofline of the dominant kernel from the library's per-kernel profile
+    (prof[k]: total ms, launches, work units over the timed region) and work
+    counters (wk), as per-launch averages: algorithmic ALU ops per launch over
+    the launch's CUDA-event time, against the ALU peak derived from unit
+    counts and the clock; DRAM bytes per launch from the ncu capture of the
+    plain workload's kernels."""
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # Both hot kernels are bound by the SM's integer ALU pipe (shifts and
+    # logic ops; ncu shows it near saturation).  Its peak, from the unit counts
+    # and clock: 152 SMs x 64 ALU lanes per cycle (16 per scheduler: half the
+    # issue rate, measured by a shift/or loop) x the maximum SM clock.
+    alu_peak = 152 * 64 * sm_max * 1e6 / 1e12            # T ALU lane-ops/s
+    # DRAM bytes per unit measured by ncu on [4, 2^32] (plain workload's kernels)
+    ncu_traffic = {"cover": 0.1270, "sieve": 0.09678} if mode == "plain" else {}
+    per = {}
+    for kern in ("sieve", "cover", "large"):
+        kp = prof[kern]
+        if kp["launches"] == 0:
+            continue
+        nl = kp["launches"]
+        ms = kp["ms"] / nl
+        if kern == "large":
+            # primes above the tile split: 2 ALU ops per strike (word index,
+            # rotated mask) issued as a global atomic AND
+            units = wk["large_strikes"] / nl
+            ops = 2.0 * units
+        elif kern == "cover" and alg_cover is not None:
+            # algorithmic work: per 64-n word, the odd primes applied until
+            # the word is full (counted by the generic cover, equal to the
+            # oracle's count); 4 ALU ops each: the 64-bit funnel shift that
+            # aligns the partner bits (2) and the OR into C (2)
+            units = float(alg_cover) * steps / nl       # alg_cover is per step
+            ops = 4.0 * units
+        elif kern == "cover":
+            # (batched mode) the block cover's own steps: 2 ops per (32-bit
+            # coverage word, prime) step, 2 per probed (n, prime)
+            units = wk["cover_iterations"] / nl
+            ops = 2.0 * units
+        else:
+            # minimal ALU work: 2 ops per strike (word index, rotated mask) and
+            # 6 per stamped 32-bit word (four pattern funnel shifts, two ANDs)
+            units = wk["sieve_strikes"] / nl
+            ops = 2.0 * units + 6.0 * (kp["units"] / nl) / 32.0
+        alg_bytes = kp["units"] / nl / 8.0               # the q bits, written once / read once
+        traffic = ncu_traffic[kern] * kp["units"] / nl if kern in ncu_traffic else None
+        achieved = ops / (ms / 1000.0) / 1e12
+        per[kern] = {"ms_per_launch": ms, "ms_total": kp["ms"], "launches": nl,
+                     "achieved": achieved, "frac": achieved / alu_peak,
+                     "alu_ops_per_launch": ops, "work_units_per_launch": units,
+                     "dram_bytes_per_launch": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+                     "hbm_frac": (alg_bytes / (ms / 1000.0)) / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)}
+    kern = max(per, key=lambda k: per[k]["ms_total"])
+    roofline = {"kernel": kern, "bound": "alu", "achieved": per[kern]["achieved"], "peak": alu_peak,
+                "unit": "T ALU lane-ops/s", "frac": per[kern]["frac"],
+                "traffic": per[kern]["dram_bytes_per_launch"],
+                "peak_source": "derived: 152 SMs x 64 ALU lanes x %.0f MHz (%s max clock)" % (sm_max, peak_src),
+                "work": ("cover: 4 ALU ops per (64-n word, odd prime) iteration until the word is full "
+                         "(algorithmic count); sieve: 2 per strike + 6 per stamped 32-bit word; "
+                         "large primes: 2 per strike"),
+                "kernels": per,
+                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
+
+    return roofline
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -614,66 +680,12 @@ def main():
 
     # ---- roofline of the dominant kernel (per-launch averages over the timed region)
     peaks, peak_src = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # Both hot kernels are bound by the SM's integer ALU pipe (shifts and
-    # logic ops; ncu shows it near saturation).  Its peak, from the unit counts
-    # and clock: 152 SMs x 64 ALU lanes per cycle (16 per scheduler: half the
-    # issue rate, measured by a shift/or loop) x the maximum SM clock.
-    alu_peak = 152 * 64 * sm_max * 1e6 / 1e12            # T ALU lane-ops/s
-    # DRAM bytes per unit measured by ncu on [4, 2^32] (plain workload's kernels)
-    ncu_traffic = {"cover": 0.1270, "sieve": 0.09678} if args.mode == "plain" else {}
-    per = {}
-    for kern in ("sieve", "cover", "large"):
-        kp = prof[kern]
-        if kp["launches"] == 0:
-            continue
-        nl = kp["launches"]
-        ms = kp["ms"] / nl
-        if kern == "large":
-            # primes above the tile split: 2 ALU ops per strike (word index,
-            # rotated mask) issued as a global atomic AND
-            units = wk["large_strikes"] / nl
-            ops = 2.0 * units
-        elif kern == "cover" and alg_cover is not None:
-            # algorithmic work: per 64-n word, the odd primes applied until
-            # the word is full (counted by the generic cover, equal to the
-            # oracle's count); 4 ALU ops each: the 64-bit funnel shift that
-            # aligns the partner bits (2) and the OR into C (2)
-            units = float(alg_cover) * args.steps / nl       # alg_cover is per step
-            ops = 4.0 * units
-        elif kern == "cover":
-            # (batched mode) the block cover's own steps: 2 ops per (32-bit
-            # coverage word, prime) step, 2 per probed (n, prime)
-            units = wk["cover_iterations"] / nl
-            ops = 2.0 * units
-        else:
-            # minimal ALU work: 2 ops per strike (word index, rotated mask) and
-            # 6 per stamped 32-bit word (four pattern funnel shifts, two ANDs)
-            units = wk["sieve_strikes"] / nl
-            ops = 2.0 * units + 6.0 * (kp["units"] / nl) / 32.0
-        alg_bytes = kp["units"] / nl / 8.0               # the q bits, written once / read once
-        traffic = ncu_traffic[kern] * kp["units"] / nl if kern in ncu_traffic else None
-        achieved = ops / (ms / 1000.0) / 1e12
-        per[kern] = {"ms_per_launch": ms, "ms_total": kp["ms"], "launches": nl,
-                     "achieved": achieved, "frac": achieved / alu_peak,
-                     "alu_ops_per_launch": ops, "work_units_per_launch": units,
-                     "dram_bytes_per_launch": traffic, "algorithmic_bytes_per_launch": alg_bytes,
-                     "hbm_frac": (alg_bytes / (ms / 1000.0)) / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)}
-    kern = max(per, key=lambda k: per[k]["ms_total"])
-    roofline = {"kernel": kern, "bound": "alu", "achieved": per[kern]["achieved"], "peak": alu_peak,
-                "unit": "T ALU lane-ops/s", "frac": per[kern]["frac"],
-                "traffic": per[kern]["dram_bytes_per_launch"],
-                "peak_source": "derived: 152 SMs x 64 ALU lanes x %.0f MHz (%s max clock)" % (sm_max, peak_src),
-                "work": ("cover: 4 ALU ops per (64-n word, odd prime) iteration until the word is full "
-                         "(algorithmic count); sieve: 2 per strike + 6 per stamped 32-bit word; "
-                         "large primes: 2 per strike"),
-                "kernels": per,
-                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
+    roofline = roofline_of(prof, wk, alg_cover, args.steps, args.mode, peaks, peak_src)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
             "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": value / (PAPER_BY_MODE[args.mode] * world) if args.mode in PAPER_BY_MODE else None,
+            "vs_baseline": value / PAPER_BY_MODE[args.mode] if args.mode in PAPER_BY_MODE else None,
             "dtype": "u64", "data": "synthetic", "mode": args.mode,
             "config": workload_desc(args.mode, world),
             "roofline": roofline,

@@ -58,3 +58,33 @@ def test_clock_sampler_takes_the_timed_window():
     c.t_start, c.t_end = 2.5, 2.6                       # a region too short to catch a sample
     r = c.stop()
     assert r["samples_in_timed_region"] == 0 and r["sm_mhz"] == 2040
+
+
+def test_roofline_arithmetic():
+    """The roofline of the bench line, from a synthetic profile: the dominant
+    kernel by total time; achieved = algorithmic ALU ops per launch over the
+    launch's time; frac = achieved / (152 SMs x 64 lanes x clock); traffic =
+    the ncu bytes per unit times the units of one launch (plain workload only)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    steps, nl = 10, 10
+    prof = {"sieve": {"ms": 19.0, "launches": nl, "units": 6.25e10},      # q bits over the timed region
+            "cover": {"ms": 23.3, "launches": nl, "units": 5.0e10},       # even n
+            "large": {"ms": 0.0, "launches": 0, "units": 0.0}}
+    wk = {"sieve_strikes": 5.3e10, "cover_iterations": 9.0e10, "large_strikes": 0.0}
+    alg_cover = 3.9e9                                                       # per step
+    peaks = {"sm_max_mhz": 2070.0, "hbm_gbs": 6695.5}
+    r = bench.roofline_of(prof, wk, alg_cover, steps, "plain", peaks, "measured")
+    peak = 152 * 64 * 2070e6 / 1e12
+    assert r["kernel"] == "cover" and r["bound"] == "alu" and abs(r["peak"] - peak) < 1e-9
+    ops = 4.0 * alg_cover * steps / nl
+    achieved = ops / (23.3 / nl / 1000.0) / 1e12
+    assert abs(r["achieved"] - achieved) < 1e-9 * achieved and abs(r["frac"] - achieved / peak) < 1e-12
+    assert abs(r["traffic"] - 0.1270 * 5.0e10 / nl) < 1e-3
+    s = r["kernels"]["sieve"]
+    assert abs(s["alu_ops_per_launch"] - (2.0 * 5.3e10 / nl + 6.0 * 6.25e10 / nl / 32.0)) < 1.0
+    assert abs(s["algorithmic_bytes_per_launch"] - 6.25e10 / nl / 8.0) < 1e-6
+    assert "large" not in r["kernels"]
+    # other workloads: the block cover's own steps, no ncu traffic
+    r2 = bench.roofline_of(prof, wk, None, steps, "batched", peaks, "measured")
+    assert r2["traffic"] is None and abs(r2["kernels"]["cover"]["alu_ops_per_launch"] - 2.0 * 9.0e10 / nl) < 1.0
