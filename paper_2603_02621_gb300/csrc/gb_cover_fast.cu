@@ -14,14 +14,16 @@
 // needs sit in registers.  A step is then
 //     s = funnel-shift of two window registers,  C |= s,  cum_k += popc(C)
 // and the histogram follows from the cumulative counts:
-// #{n : p_min(n) = p_k} = cum_k - cum_{k-1}.  Block 0 (L0 primes) runs on
+// #{n : p_min(n) = p_k} = cum_k - cum_{k-1} (three counts per register, added
+// by multiply-adds with the field weights).  Block 0 (L0 primes) runs on
 // every word of the CTA, three consecutive words per lane sharing one window;
 // the words it leaves open (about one in three after 48 primes near 1e10) go
 // to per-warp lists in shared memory, and blocks of 32 primes run on the open
 // words alone, each leaving a shorter list, so that every lane of every step
 // still works on an open word.  The prefix KA = L0 + 32 x (later blocks).
 //
-// Probing.  The few n open after the last block (about 1 in 10^5 near 1e10)
+// Probing.  The few n open after the last block (about 1 in 10^4 after 112
+// primes near 1e10)
 // are taken one at a time by a warp: lane t probes the bit of Q at j + d_k for
 // k = k0 + t, and the lowest set bit of the ballot is p_min.  An n still open
 // after K primes goes to the retry pass (or counts as unresolved).
@@ -134,10 +136,10 @@ __device__ __forceinline__ void flush_block(const uint32_t (&cum)[KH], uint32_t 
 }
 
 // ---------------------------------------------------------------------------
-// block 0 on three consecutive words per lane.  The histogram needs, per step,
-// popc(C0) + popc(C1) + popc(C2); a carry-save adder gives it with two
-// popcounts: ones = C0 ^ C1 ^ C2, twos = majority(C0, C1, C2), and
-// popc(C0) + popc(C1) + popc(C2) = popc(ones) + 2 popc(twos).
+// block 0 on three consecutive words per lane: one window serves the three
+// words, so a step is three funnel shifts, three ORs and the three words'
+// popcounts added into the step's counter.  (A carry-save adder would need
+// two popcounts instead of three, at two more logic ops; measured the same.)
 // Window: R[t] = Q32[w + 2 + d_3/32 - t] for the lane's first word w.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int block0_regs3(int L0) { return (int)((step_e(L0 - 1) + 31) / 32) + 3; }
