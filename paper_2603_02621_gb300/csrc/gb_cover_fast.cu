@@ -711,6 +711,7 @@ int cover_fast_phase_primes(uint32_t K, uint64_t n_hi)
     // about 0.05, after 112 about 0.003
     int ka = n_hi < 100000000000ull ? 112 : n_hi < 10000000000000000ull ? 128 : 176;
     while (ka >= 48 && (uint32_t)ka > K) ka -= 32;
+    if (ka < 48 && K >= 48) ka = 48;                        // the shortest schedule, block 0 alone
     return ka >= 48 ? ka : 0;
 }
 
