@@ -2,24 +2,24 @@
 
 Modes (--mode), each a workload of GoldbachGPU (arXiv 2603.02621):
 
-* plain (default): exhaustive verification of every even n in [4, 10^10]
-  (Table 4's workload): one step = one gb_verify_range call: segment sieve of
-  the q window, the loop-inverted cover with P1 = 2^15, the GPU retry pass to
-  P2 = 2^20, per-segment reductions (Sec. 2.3);
-* exhaustive-1e12: [4, 10^12] (Table 4's largest range), segments of 2^27 even n,
-  base primes to 2^31;
-* window-4e18: the 10^11-wide window [4e18 - 10^11, 4e18), segments of 2^27;
-* batched: 4096 ranges of uneven length (log-uniform 2^10..2^26 even n) and
-  offset (uniform in [10^9, 10^15]) in one gb_verify_batch call after the
-  autotuner has picked tile, split, P1 and cover prefix; the plain per-range
-  launch loop over the same ranges, with the same outputs, is timed beside it.
+* exhaustive-1e12 (default): exhaustive verification of every even n in
+  [4, 10^12] (Table 4's largest range, the paper's headline): one step = one
+  gb_verify_range call over the range -- segments of 2^27 even n, base primes
+  to 2^31, the segment sieve of the q window, the loop-inverted cover with
+  P1 = 2^15, the GPU retry pass to P2 = 2^20, per-segment reductions
+  (Sec. 2.3).  The same line carries, as extra keys, the 10^11-wide window
+  [4e18 - 10^11, 4e18) (``window_4e18``) and the 4096-range batch against the
+  per-range launch loop over the same ranges (``batched``);
+* plain: [4, 10^10], segments of 2^24 even n;
+* window-4e18, batched, serving: one of those workloads alone.
 
-Multi-GPU (torchrun): each rank verifies its own shard (plain family: the next
-range of the same width; batched: its own 4096 ranges) -- independent work, no
-collective on the data path (weak scaling); the timing is the max over ranks.
+Multi-GPU (torchrun): plain family -- the range is cut into contiguous runs of
+whole segments, one per rank (strong scaling; the ranks' totals are merged by
+one gather after timing, the only exchange); batched -- each rank its own 4096
+ranges (weak scaling).  The timing is the max over ranks.
 
---impl reference times the CPU oracle (oracle/) on a bounded sample of the
-same workload, on the host cores.
+--impl reference times the CPU oracle (oracle/) on seeded units of the same
+workload (whole segments of the range), on the host cores.
 """
 from __future__ import annotations
 
@@ -40,26 +40,34 @@ METRIC = "even integers verified/sec"
 UNIT = "even n/s"
 P1, P2 = 1 << 15, 1 << 20
 HL = 3512                           # pi(2^15): histogram row length
-PAPER_NPS = 4999999999 / 23.547     # Table 4: [4, 1e10] in 23,547 ms on an RTX 3070
-# the paper's number for the same workload, where it has one (Table 4, RTX 3070)
-PAPER_BY_MODE = {"plain": PAPER_NPS, "exhaustive-1e12": 499999999999 / 2457.040}
+# the paper's number for the same workload (Table 4, one RTX 3070)
+PAPER_BY_MODE = {"plain": 4999999999 / 23.547, "exhaustive-1e12": 499999999999 / 2457.040}
 PAPER_CONTEXT = ("RTX 3070 (8 GB), Table 4: [4, 1e10] in 23,547 ms = 2.12e8 n/s; "
                  "[4, 1e12] in 2,457,040 ms = 2.03e8 n/s")
+DEFAULT_MODE = "exhaustive-1e12"
 
-# plain-family workloads: (first range, shift per rank, segment length, base primes)
+# plain-family workloads: (range, segment length, base primes)
 PLAIN_MODES = {
-    "plain": dict(lo=4, hi=10**10 + 2, shift=10**10, seg=1 << 24, base=None,
-                  workload="exhaustive Goldbach verification of every even n in [4, 1e10] per GPU"),
-    "exhaustive-1e12": dict(lo=4, hi=10**12 + 2, shift=10**12, seg=1 << 27, base=1 << 31,
-                            workload="exhaustive Goldbach verification of every even n in [4, 1e12] per GPU"),
-    "window-4e18": dict(lo=4 * 10**18 - 10**11, hi=4 * 10**18, shift=-10**11, seg=1 << 27, base=1 << 31,
-                        workload="Goldbach verification of the window [4e18 - 1e11, 4e18) per GPU"),
+    "plain": dict(lo=4, hi=10**10 + 2, seg=1 << 24, base=None,
+                  workload="exhaustive Goldbach verification of every even n in [4, 1e10]"),
+    "exhaustive-1e12": dict(lo=4, hi=10**12 + 2, seg=1 << 27, base=1 << 31,
+                            workload="exhaustive Goldbach verification of every even n in [4, 1e12]"),
+    "window-4e18": dict(lo=4 * 10**18 - 10**11, hi=4 * 10**18, seg=1 << 27, base=1 << 31,
+                        workload="Goldbach verification of every even n in the window [4e18 - 1e11, 4e18)"),
+}
+# DRAM bytes per unit (even n) of the dominant kernels, from ncu captures
+# (profiles/): scaled to a launch by the units it processes
+NCU_TRAFFIC = {
+    "plain": {"cover": 0.1270, "sieve": 0.09678},
 }
 
 
-def rank_range(mode: str, rank: int):
+def rank_range(mode: str, rank: int, world: int = 1):
+    """[a, b) of rank `rank`: the whole range at N = 1, else a contiguous run
+    of whole segments (strong scaling)."""
+    from paper_2603_02621_gb300 import shard
     m = PLAIN_MODES[mode]
-    return m["lo"] + rank * m["shift"], m["hi"] + rank * m["shift"]
+    return shard.shard_range(m["lo"], m["hi"], m["seg"], world, rank)
 
 
 def base_for(mode: str, hi: int) -> int:
@@ -80,13 +88,13 @@ def workload_desc(mode: str, world: int):
                 "tuning": "gb_autotune on the same batch before timing",
                 "l2": "batch q buffer ~3.1 GB > 126 MB L2; no flush needed"}
     m = PLAIN_MODES[mode]
-    lo, hi = rank_range(mode, 0)
-    n = (hi - lo) // 2
-    return {"workload": m["workload"], "ranges": [list(rank_range(mode, r)) for r in range(world)],
-            "seg_len": m["seg"], "base_primes_to": base_for(mode, hi) if m["base"] else "isqrt(hi)+ (>= 1e5)",
+    n = (m["hi"] - m["lo"]) // 2
+    return {"workload": m["workload"], "range": [m["lo"], m["hi"]], "even_n": n,
+            "rank_ranges": [list(rank_range(mode, r, world)) for r in range(world)],
+            "seg_len": m["seg"], "base_primes_to": base_for(mode, m["hi"]) if m["base"] else "isqrt(hi)+ (>= 1e5)",
             "p1": P1, "p2": P2,
             "outputs": f"per-segment p_min histogram ({HL} entries), max p_min with n, unresolved",
-            "l2": f"q window {n / 8 / 1e6:.0f} MB per GPU > 126 MB L2; no flush needed"}
+            "l2": f"q window {min(n, 1 << 33) / 8 / 1e6:.0f} MB per slab > 126 MB L2; no flush needed"}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -194,16 +202,16 @@ def barrier(world: int, backend_ready: bool):
 # ----------------------------------------------------------------------------- cpu baseline
 def sample_units(mode: str, seed: int = 11):
     """The workload cut into independent units (lo, hi) the oracle can verify
-    one by one, in a seeded random order: segments for the plain family,
-    ranges for the batched mode."""
+    one by one, in a seeded random order: the range's segments for the plain
+    family, the ranges for the batched mode."""
     from paper_2603_02621_gb300 import workloads
     if mode == "batched":
         units = workloads.batched_ranges(count=4096, seed=1)
     elif mode == "serving":
         units = [(a, b) for t, kind, a, b in workloads.serving_stream(count=2000, seed=7) if kind == "range"]
     else:
-        lo, hi = rank_range(mode, 0)
-        seg = PLAIN_MODES[mode]["seg"]
+        m = PLAIN_MODES[mode]
+        lo, hi, seg = m["lo"], m["hi"], m["seg"]
         units = [(a, min(a + 2 * seg, hi)) for a in range(lo, hi, 2 * seg)]
     rng = workloads.SplitMix64(seed)
     order = list(range(len(units)))
@@ -213,54 +221,79 @@ def sample_units(mode: str, seed: int = 11):
     return [units[i] for i in order]
 
 
-def cpu_baseline(mode: str = "plain", min_seconds: float = 12.0, seed: int = 11):
-    """The oracle, as it stands, on a bounded sample of the workload's units
-    (one unit per host thread at a time)."""
-    from oracle import oracle
-    import concurrent.futures as cf
-    threads = oracle.default_threads()
-    units = sample_units(mode, seed)
-    if mode != "plain":
-        oracle.primes_upto(3)                           # (cached small primes are built on first use)
-        lo_max = max(b for _, b in units)
-        oracle.verify_segments(lo_max - 4, lo_max, 2, P2, 8, threads=1)   # warm the prime cache untimed
+def unit_kind(mode: str) -> str:
+    if mode in PLAIN_MODES:
+        m = PLAIN_MODES[mode]
+        return "segments of %d even n of [%d, %d)" % (m["seg"], m["lo"], m["hi"])
+    return {"batched": "ranges of the 4096-range batch", "serving": "range requests of the serving stream"}[mode]
 
-    def one(u):
+
+class OracleRunner:
+    """The oracle, as it stands, on seeded units of the workload: one unit per
+    host thread at a time, each verified by the oracle in one thread."""
+
+    def __init__(self, mode: str, seed: int = 11):
+        from oracle import oracle
+        import concurrent.futures as cf
+        self.oracle = oracle
+        self.mode = mode
+        self.threads = oracle.default_threads()
+        self.units = sample_units(mode, seed)
+        self.used = 0
+        self.ex = cf.ThreadPoolExecutor(max_workers=self.threads)
+        if mode != "plain":
+            hi_max = max(b for _, b in self.units)
+            oracle.verify_segments(hi_max - 4, hi_max, 2, P2, 8, threads=1)   # the prime cache, untimed
+
+    def _one(self, u):
         a, b = u
-        n = (b - a) // 2
-        s, _ = oracle.verify_segments(a, b, n, P2, HL, threads=1)
+        s, _ = self.oracle.verify_segments(a, b, (b - a) // 2, P2, HL, threads=1)
         return int(s[:, 0].sum())
 
-    done_n, t0, used = 0, time.perf_counter(), 0
-    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        while time.perf_counter() - t0 < min_seconds and used < len(units):
-            batch = units[used:used + threads]
-            done_n += sum(ex.map(one, batch))
-            used += len(batch)
-    dt = time.perf_counter() - t0
-    kind = {"batched": "ranges of the 4096-range batch", "serving": "range requests of the serving stream"}.get(
-        mode, "segments of %d even n of [%d, %d)" % ((PLAIN_MODES[mode]["seg"],) + tuple(rank_range(mode, 0))))
-    return {"value": done_n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "value_per_core": done_n / dt / threads,
-            "sample": f"{used} seeded {kind} ({done_n} n, {dt:.1f} s wall, P = 2^20)",
-            "seconds": dt}
+    def step(self):
+        """One batch of `threads` units (wrapping around the sample): returns
+        (even n verified, wall seconds)."""
+        batch = [self.units[(self.used + k) % len(self.units)] for k in range(self.threads)]
+        self.used += len(batch)
+        t0 = time.perf_counter()
+        n = sum(self.ex.map(self._one, batch))
+        return n, time.perf_counter() - t0
+
+    def close(self):
+        self.ex.shutdown()
 
 
-def roofline_of(prof, wk, alg_cover, steps, mode, peaks, peak_src):
+def cpu_baseline(mode: str = "plain", min_seconds: float = 12.0, seed: int = 11):
+    """The oracle on a bounded sample of the workload's units: batches of one
+    unit per host thread until min_seconds of wall time have passed."""
+    r = OracleRunner(mode, seed)
+    done_n, wall, steps = 0, 0.0, 0
+    while wall < min_seconds and r.used < len(r.units):
+        n, dt = r.step()
+        done_n += n
+        wall += dt
+        steps += 1
+    r.close()
+    return {"value": done_n / wall, "unit": UNIT, "cores": r.threads, "kind": "oracle",
+            "value_per_core": done_n / wall / r.threads,
+            "sample": f"{r.used} seeded {unit_kind(mode)} ({done_n} n, {wall:.1f} s wall, P = 2^20)",
+            "seconds": wall}
+
+
+def roofline_of(prof, wk, alg_cover, steps, mode, peaks, peak_src, sms):
     """Roofline of the dominant kernel from the library's per-kernel profile
     (prof[k]: total ms, launches, work units over the timed region) and work
     counters (wk), as per-launch averages: algorithmic ALU ops per launch over
-    the launch's CUDA-event time, against the ALU peak derived from unit
-    counts and the clock; DRAM bytes per launch from the ncu capture of the
-    plain workload's kernels."""
+    the launch's CUDA-event time, against the ALU peak derived from the
+    device's SM count, the ALU lanes per SM and the clock; DRAM bytes per
+    launch from an ncu capture of the same kernel (NCU_TRAFFIC)."""
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     # Both hot kernels are bound by the SM's integer ALU pipe (shifts and
     # logic ops; ncu shows it near saturation).  Its peak, from the unit counts
-    # and clock: 152 SMs x 64 ALU lanes per cycle (16 per scheduler: half the
+    # and clock: SMs x 64 ALU lanes per cycle (16 per scheduler: half the
     # issue rate, measured by a shift/or loop) x the maximum SM clock.
-    alu_peak = 152 * 64 * sm_max * 1e6 / 1e12            # T ALU lane-ops/s
-    # DRAM bytes per unit measured by ncu on [4, 2^32] (plain workload's kernels)
-    ncu_traffic = {"cover": 0.1270, "sieve": 0.09678} if mode == "plain" else {}
+    alu_peak = sms * 64 * sm_max * 1e6 / 1e12            # T ALU lane-ops/s
+    ncu_traffic = NCU_TRAFFIC.get(mode, {})
     per = {}
     for kern in ("sieve", "cover", "large"):
         kp = prof[kern]
@@ -270,7 +303,7 @@ def roofline_of(prof, wk, alg_cover, steps, mode, peaks, peak_src):
         ms = kp["ms"] / nl
         if kern == "large":
             # primes above the tile split: 2 ALU ops per strike (word index,
-            # rotated mask) issued as a global atomic AND
+            # rotated mask) issued as an atomic AND
             units = wk["large_strikes"] / nl
             ops = 2.0 * units
         elif kern == "cover" and alg_cover is not None:
@@ -299,40 +332,46 @@ def roofline_of(prof, wk, alg_cover, steps, mode, peaks, peak_src):
                      "dram_bytes_per_launch": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                      "hbm_frac": (alg_bytes / (ms / 1000.0)) / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)}
     kern = max(per, key=lambda k: per[k]["ms_total"])
-    roofline = {"kernel": kern, "bound": "alu", "achieved": per[kern]["achieved"], "peak": alu_peak,
-                "unit": "T ALU lane-ops/s", "frac": per[kern]["frac"],
-                "traffic": per[kern]["dram_bytes_per_launch"],
-                "peak_source": "derived: 152 SMs x 64 ALU lanes x %.0f MHz (%s max clock)" % (sm_max, peak_src),
-                "work": ("cover: 4 ALU ops per (64-n word, odd prime) iteration until the word is full "
-                         "(algorithmic count); sieve: 2 per strike + 6 per stamped 32-bit word; "
-                         "large primes: 2 per strike"),
-                "kernels": per,
-                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
-
-    return roofline
+    return {"kernel": kern, "bound": "alu", "achieved": per[kern]["achieved"], "peak": alu_peak,
+            "unit": "T ALU lane-ops/s", "frac": per[kern]["frac"],
+            "traffic": per[kern]["dram_bytes_per_launch"],
+            "peak_source": "derived: %d SMs (device attribute) x 64 ALU lanes x %.0f MHz (%s max clock)"
+                           % (sms, sm_max, peak_src),
+            "work": ("cover: 4 ALU ops per (64-n word, odd prime) iteration until the word is full "
+                     "(algorithmic count); sieve: 2 per strike + 6 per stamped 32-bit word; "
+                     "large primes: 2 per strike"),
+            "kernels": per,
+            "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
 
 
 def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step one batch of seeded units of
+    the workload (one whole segment per host thread), timed on the wall clock;
+    value = even n verified in the timed steps / their wall time."""
     if rank != 0:
         return 0
-    per_step = max(4.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    mode = args.mode
+    r = OracleRunner(mode)
     for _ in range(args.warmup):
-        cpu_baseline(args.mode, min_seconds=1.0)
-    vals = []
-    last = None
+        r.step()
+    done_n, wall = 0, 0.0
     for _ in range(args.steps):
-        last = cpu_baseline(args.mode, min_seconds=per_step)
-        vals.append(last["value"])
-    value = statistics.mean(vals)
-    n_step = workload_n(args.mode)
+        n, dt = r.step()
+        done_n += n
+        wall += dt
+    r.close()
+    value = done_n / wall
+    sample = (f"{args.steps} steps of {r.threads} seeded {unit_kind(mode)} each "
+              f"({done_n} n verified in {wall:.1f} s wall, P = 2^20)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * n_step / value,
-            "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": value / PAPER_BY_MODE[args.mode] if args.mode in PAPER_BY_MODE else None,
-            "dtype": "u64", "data": "synthetic", "mode": args.mode, "config": workload_desc(args.mode, 1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                             "value_per_core": value / last["cores"], "sample": last["sample"]},
+            "ms_per_step": 1000.0 * wall / max(1, args.steps),
+            "n_per_step": done_n / max(1, args.steps),
+            "higher_is_better": True, "scaling": "strong" if mode in PLAIN_MODES else "weak",
+            "vs_baseline": value / PAPER_BY_MODE[mode] if mode in PAPER_BY_MODE else None,
+            "dtype": "u64", "data": "synthetic", "mode": mode, "config": workload_desc(mode, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r.threads, "kind": "oracle",
+                             "value_per_core": value / r.threads, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -346,34 +385,37 @@ def workload_n(mode: str, rank: int = 0) -> int:
     if mode == "batched":
         from paper_2603_02621_gb300 import workloads
         return sum((b - a) // 2 for a, b in workloads.batched_ranges(count=4096, seed=1 + rank))
-    lo, hi = rank_range(mode, rank)
-    return (hi - lo) // 2
+    m = PLAIN_MODES[mode]
+    return (m["hi"] - m["lo"]) // 2
 
 
 # ----------------------------------------------------------------------------- workloads on the GPU
 class PlainWork:
-    """One gb_verify_range call over the rank's range per step."""
+    """One gb_verify_range call over the rank's share of the range per step."""
 
-    def __init__(self, gb, torch, mode, rank, local, stream):
+    def __init__(self, gb, torch, mode, rank, world, local, stream, parent=None):
         self.gb = gb
-        self.lo, self.hi = rank_range(mode, rank)
+        self.mode = mode
+        self.lo, self.hi = rank_range(mode, rank, world)
         self.seg = PLAIN_MODES[mode]["seg"]
-        self.ctx = gb.Context(device=local, base_limit=base_for(mode, self.hi), seg_len=self.seg,
-                              p1=P1, p2=P2, stream=stream.cuda_stream)
-        self.nseg = ((self.hi - self.lo) // 2 + self.seg - 1) // self.seg
+        if parent is not None and parent.config()["base_limit"] >= base_for(mode, PLAIN_MODES[mode]["hi"]):
+            self.ctx = parent.share(stream.cuda_stream)
+            self.ctx.set_config(seg_len=self.seg, p1=P1, p2=P2)
+        else:
+            self.ctx = gb.Context(device=local, base_limit=base_for(mode, PLAIN_MODES[mode]["hi"]),
+                                  seg_len=self.seg, p1=P1, p2=P2, stream=stream.cuda_stream)
         self.n = (self.hi - self.lo) // 2
+        self.nseg = max(1, (self.n + self.seg - 1) // self.seg)
         # device-resident outputs for the device-timed value, pinned host ones for e2e
         self.d_rows = torch.zeros((self.nseg, HL), dtype=torch.int64, device="cuda")
         self.d_segs = torch.zeros((self.nseg, 6), dtype=torch.int64, device="cuda")    # 48-byte records
         self.h_rows = torch.zeros((self.nseg, HL), dtype=torch.int64).pin_memory()
         self.h_segs = torch.zeros((self.nseg, 6), dtype=torch.int64).pin_memory()
         self.h_hist = torch.zeros(HL, dtype=torch.int64).pin_memory()
-        self.h2d = 0
-        self.d2h = 32 + self.nseg * 48 + self.nseg * HL * 8 + HL * 8
         self.last = None
         self.tuned = None
 
-    def autotune(self, torch):
+    def autotune(self):
         """gb_autotune on the rank's own range (plain mode), before timing."""
         cfg, ms = self.ctx.autotune([(self.lo, self.hi)], self.gb.GB_TUNE_PLAIN, reps=1)
         # per-segment outputs follow seg_len: keep the workload's
@@ -383,6 +425,8 @@ class PlainWork:
 
     def _call(self, rows, segs, hist):
         gb = self.gb
+        if self.n == 0:
+            return None
         r = gb.gb_range_result()
         r.seg_hist = ctypes_ptr(rows)
         r.seg_hist_stride = HL
@@ -403,10 +447,15 @@ class PlainWork:
     def step_host(self):
         return self._call(self.h_rows, self.h_segs, self.h_hist)
 
-    def check(self):
+    def totals(self):
+        """The rank's totals of the last host step (for the merge)."""
+        import numpy as np
         r = self.last
-        return {"unresolved": int(r.unresolved), "max_pmin": int(r.max_pmin),
-                "max_pmin_n": int(r.max_pmin_n), "n_checked": int(r.n_checked)}
+        if r is None:
+            return {"n_checked": 0, "unresolved": 0, "max_pmin": 0, "max_pmin_n": 0,
+                    "hist": np.zeros(HL, dtype=np.uint64)}
+        return {"n_checked": int(r.n_checked), "unresolved": int(r.unresolved), "max_pmin": int(r.max_pmin),
+                "max_pmin_n": int(r.max_pmin_n), "hist": self.h_hist.numpy().view(np.uint64).copy()}
 
     def algorithmic_cover_iterations(self):
         """The cover's algorithmic work for one step (untimed): the generic
@@ -414,6 +463,8 @@ class PlainWork:
         until the word is full -- equal to the oracle's count from the p_min
         values (tests/test_gpu_work.py)."""
         gb = self.gb
+        if self.n == 0:
+            return 0
         saved = self.ctx.config()["cover_prefix"]
         self.ctx.set_config(cover_prefix=1)
         gb.gb_profile_enable(self.ctx.handle, True)
@@ -423,7 +474,7 @@ class PlainWork:
         self.ctx.set_config(cover_prefix=saved)
         return iters
 
-    def extra(self, args):
+    def extra(self):
         if self.tuned is None:
             return {}
         return {"autotuned": self.tuned[0], "autotune_best_ms": self.tuned[1]}
@@ -432,9 +483,10 @@ class PlainWork:
 class BatchWork:
     """One gb_verify_batch call over the rank's 4096 ranges per step."""
 
-    def __init__(self, gb, torch, mode, rank, local, stream):
+    def __init__(self, gb, torch, rank, local, stream):
         from paper_2603_02621_gb300 import workloads
         self.gb, self.torch = gb, torch
+        self.mode = "batched"
         self.ranges = workloads.batched_ranges(count=4096, seed=1 + rank)
         self.count = len(self.ranges)
         self.n = sum((b - a) // 2 for a, b in self.ranges)
@@ -446,8 +498,6 @@ class BatchWork:
         self.d_rows = torch.zeros((self.count, HL), dtype=torch.int64, device="cuda")
         self.h_res = torch.zeros((self.count, 6), dtype=torch.int64).pin_memory()
         self.h_rows = torch.zeros((self.count, HL), dtype=torch.int64).pin_memory()
-        self.h2d = 0                       # the range list is host memory the call reads (count x 16 B)
-        self.d2h = self.count * 48 + self.count * HL * 8
         self.tuned, self.tune_ms = self.ctx.autotune(self.ranges, gb.GB_TUNE_BATCH, reps=1)
 
     def _call(self, res, rows):
@@ -472,10 +522,13 @@ class BatchWork:
         return {"unresolved": unres, "max_pmin": int(mp[k]), "max_pmin_n": int(raw[k, 4]),
                 "n_checked": int(raw[:, 2].sum())}
 
-    def extra(self, args):
+    def algorithmic_cover_iterations(self):
+        return None
+
+    def extra(self):
         """The plain per-range launch loop over the same ranges, same outputs
         (per-range totals and histogram row, device-resident), timed once after
-        one warm-up pass; and the batch without its CUDA graph."""
+        one warm-up pass, with CUDA events on the context's stream."""
         gb, torch = self.gb, self.torch
         d_hist = torch.zeros((self.count, HL), dtype=torch.int64, device="cuda")
         lib = gb.load()
@@ -491,16 +544,87 @@ class BatchWork:
 
         loop()
         torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        ev0.record(stream)
         loop()
+        ev1.record(stream)
         torch.cuda.synchronize()
-        loop_s = time.perf_counter() - t0
+        wall_s = time.perf_counter() - t0
+        loop_ms = ev0.elapsed_time(ev1)
         same = bool(torch.equal(d_hist, self.d_rows))
-        return {"plain_loop": {"value": self.n / loop_s, "unit": UNIT, "ms": 1000.0 * loop_s,
+        return {"plain_loop": {"value": self.n / (loop_ms / 1000.0), "unit": UNIT, "ms": loop_ms,
+                               "wall_ms": 1000.0 * wall_s,
                                "launch": "gb_verify_range per range, same per-range histograms",
                                "same_histograms": same},
-                "autotuned": {k: self.tuned[k] for k in ("tile_bits", "bucket_split", "p1", "cover_prefix")},
+                "autotuned": {k: self.tuned[k] for k in ("tile_bits", "bucket_split", "cta_threads", "p1",
+                                                         "cover_prefix")},
                 "autotune_best_ms": self.tune_ms}
+
+
+def measure(work, gb, torch, stream, steps, warmup, world, backend_ready, peaks, peak_src, sms, clocks=None):
+    """Warm-up, then `steps` steps timed with CUDA events on the context's
+    stream (device-resident outputs, per-kernel profile), then `steps` steps
+    through the same public call with pinned host outputs on the wall clock
+    (e2e, with the bytes the calls copied between host and device)."""
+    ctx = work.ctx
+    alg_cover = work.algorithmic_cover_iterations()
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        work.step_device()
+    torch.cuda.synchronize()
+
+    gb.gb_profile_enable(ctx.handle, True)
+    barrier(world, backend_ready)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.mark_start()
+    ev0.record(stream)
+    for _ in range(steps):
+        work.step_device()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world, backend_ready)
+    dev_ms = ev0.elapsed_time(ev1)
+    prof = gb.gb_profile_read(ctx.handle)
+    wk = gb.gb_profile_work(ctx.handle)
+    launches = gb.gb_profile_kernels(ctx.handle)
+    gb.gb_profile_enable(ctx.handle, False)            # (also resets the copy counters)
+    max_ms = reduce_max(dev_ms, world, backend_ready)
+
+    barrier(world, backend_ready)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        work.step_host()
+    torch.cuda.synchronize()
+    e2e_ms = 1000.0 * (time.perf_counter() - t0)
+    if clocks:
+        clocks.mark_end()
+    copies = gb.gb_profile_copies(ctx.handle)
+    e2e_ms = reduce_max(e2e_ms, world, backend_ready)
+
+    n_all = workload_n(work.mode) if work.mode in PLAIN_MODES else work.n * world
+    total_n = n_all * steps
+    return {"value": total_n / (max_ms / 1000.0), "ms_per_step": max_ms / steps, "steps": steps, "warmup": warmup,
+            "e2e": {"value": total_n / (e2e_ms / 1000.0), "unit": UNIT,
+                    "h2d_bytes_per_step": copies["h2d"] / steps, "d2h_bytes_per_step": copies["d2h"] / steps,
+                    "copies": "counted by the library (gb_profile_copies) over the e2e steps"},
+            "roofline": roofline_of(prof, wk, alg_cover, steps, work.mode, peaks, peak_src, sms),
+            "gpu_launches": int(launches), "kernel_ms": {k: prof[k]["ms"] for k in prof},
+            "algorithmic_cover_iterations_per_step": alg_cover}
+
+
+def merged_check(work, world, backend_ready):
+    """Totals of the whole range (plain family): the ranks' totals of their
+    last host step, merged by one gather (the only exchange)."""
+    from paper_2603_02621_gb300 import shard
+    local = work.totals()
+    tot = shard.gather_merge(local, HL) if world > 1 and backend_ready else local
+    return {"n_checked": int(tot["n_checked"]), "unresolved": int(tot["unresolved"]),
+            "max_pmin": int(tot["max_pmin"]), "max_pmin_n": int(tot["max_pmin_n"])}
 
 
 # ----------------------------------------------------------------------------- serving
@@ -598,7 +722,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="plain", choices=sorted(PLAIN_MODES) + ["batched", "serving"])
+    ap.add_argument("--mode", default=DEFAULT_MODE, choices=sorted(PLAIN_MODES) + ["batched", "serving"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default mode: skip the window and batched measurements carried as extra keys")
+    ap.add_argument("--extra-steps", type=int, default=10, help="timed steps of each extra workload")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the timed stream")
     ap.add_argument("--lanes", type=int, default=2, help="serving: server lanes")
     ap.add_argument("--hbm-budget", type=int, default=0, help="serving: admission budget, GiB (0: half the free HBM)")
@@ -608,6 +735,10 @@ def main():
     ap.add_argument("--hi", type=int, default=None, help="custom range end")
     args = ap.parse_args()
     world, rank, local = dist_setup()
+    if args.lo is not None and args.hi is not None and args.mode in PLAIN_MODES:
+        PLAIN_MODES[args.mode].update(lo=args.lo, hi=args.hi,
+                                      workload=f"exhaustive Goldbach verification of every even n in "
+                                               f"[{args.lo}, {args.hi})")
     if args.impl == "reference":
         return run_reference(args, world, rank)
 
@@ -623,85 +754,59 @@ def main():
     stream = torch.cuda.current_stream()
     if args.mode == "serving":
         return run_serving(args, gb, torch, world, rank, local, backend_ready)
+    peaks, peak_src = load_peaks()
+    sms = int(torch.cuda.get_device_properties(local).multi_processor_count)
     if args.mode == "batched":
-        work = BatchWork(gb, torch, args.mode, rank, local, stream)
+        work = BatchWork(gb, torch, rank, local, stream)
     else:
-        if args.lo is not None and args.hi is not None:
-            PLAIN_MODES[args.mode].update(lo=args.lo, hi=args.hi, shift=args.hi - args.lo)
-        work = PlainWork(gb, torch, args.mode, rank, local, stream)
+        work = PlainWork(gb, torch, args.mode, rank, world, local, stream)
         if args.autotune:
-            work.autotune(torch)
-    ctx = work.ctx
+            work.autotune()
 
-    alg_cover = work.algorithmic_cover_iterations() if isinstance(work, PlainWork) else None
-    torch.cuda.synchronize()
     # clocks are sampled from the warm-up through the timed and end-to-end regions
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.2)
-    for _ in range(args.warmup):
-        work.step_device()
-    torch.cuda.synchronize()
-
-    # ---- device-timed region (value), per-kernel events
-    gb.gb_profile_enable(ctx.handle, True)
-    barrier(world, backend_ready)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks.mark_start()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        work.step_device()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world, backend_ready)
-    dev_ms = ev0.elapsed_time(ev1)
-    prof = gb.gb_profile_read(ctx.handle)
-    wk = gb.gb_profile_work(ctx.handle)
-    launches = gb.gb_profile_kernels(ctx.handle)
-    gb.gb_profile_enable(ctx.handle, False)
-    max_ms = reduce_max(dev_ms, world, backend_ready)
-
-    # ---- end-to-end region through the public call with pinned host buffers
-    barrier(world, backend_ready)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        work.step_host()
-    torch.cuda.synchronize()
-    e2e_ms = 1000.0 * (time.perf_counter() - t0)
-    clocks.mark_end()
+    m = measure(work, gb, torch, stream, args.steps, args.warmup, world, backend_ready, peaks, peak_src, sms,
+                clocks)
     clk = clocks.stop()
-    e2e_ms = reduce_max(e2e_ms, world, backend_ready)
-
-    total_n = work.n * args.steps * world
-    value = total_n / (max_ms / 1000.0)
-    e2e_value = total_n / (e2e_ms / 1000.0)
-
-    # ---- roofline of the dominant kernel (per-launch averages over the timed region)
-    peaks, peak_src = load_peaks()
-    roofline = roofline_of(prof, wk, alg_cover, args.steps, args.mode, peaks, peak_src)
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": value / PAPER_BY_MODE[args.mode] if args.mode in PAPER_BY_MODE else None,
+    check = work.check() if args.mode == "batched" else merged_check(work, world, backend_ready)
+    plain_family = args.mode in PLAIN_MODES
+    line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+            "higher_is_better": True, "scaling": "strong" if plain_family else "weak",
+            "vs_baseline": m["value"] / PAPER_BY_MODE[args.mode] if args.mode in PAPER_BY_MODE else None,
             "dtype": "u64", "data": "synthetic", "mode": args.mode,
             "config": workload_desc(args.mode, world),
-            "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": work.h2d,
-                    "d2h_bytes_per_step": work.d2h},
-            "clocks": clk,
-            "gpu_launches": int(launches),
-            "kernel_ms": {k: prof[k]["ms"] for k in prof},
-            "result_check": work.check(),
-            "paper_context": PAPER_CONTEXT}
-    line.update(work.extra(args))
+            "roofline": m["roofline"], "e2e": m["e2e"], "clocks": clk,
+            "gpu_launches": m["gpu_launches"], "sm_count": sms, "kernel_ms": m["kernel_ms"],
+            "result_check": check, "paper_context": PAPER_CONTEXT}
+    line.update(work.extra())
+
+    # the same line carries the other config-4 window and the batched mode
+    if args.mode == DEFAULT_MODE and not args.no_extras:
+        xs = max(1, args.extra_steps)
+        wwork = PlainWork(gb, torch, "window-4e18", rank, world, local, stream, parent=work.ctx)
+        wm = measure(wwork, gb, torch, stream, xs, 3, world, backend_ready, peaks, peak_src, sms)
+        line["window_4e18"] = {**{k: wm[k] for k in ("value", "ms_per_step", "steps", "warmup", "e2e", "roofline",
+                                                     "gpu_launches", "kernel_ms")},
+                               "unit": UNIT, "scaling": "strong", "config": workload_desc("window-4e18", world),
+                               "result_check": merged_check(wwork, world, backend_ready)}
+        wwork.ctx.close()
+        bwork = BatchWork(gb, torch, rank, local, stream)
+        bm = measure(bwork, gb, torch, stream, xs, 3, world, backend_ready, peaks, peak_src, sms)
+        bx = bwork.extra()
+        line["batched"] = {**{k: bm[k] for k in ("value", "ms_per_step", "steps", "warmup", "e2e", "roofline",
+                                                 "gpu_launches", "kernel_ms")},
+                           "unit": UNIT, "scaling": "weak", "config": workload_desc("batched", world),
+                           "result_check": bwork.check(), **bx,
+                           "faster_than_plain_loop": bm["value"] > bx["plain_loop"]["value"]}
+        bwork.ctx.close()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(args.mode).items() if k != "seconds"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
+    work.ctx.close()
     if backend_ready:
         import torch.distributed as dist
         dist.destroy_process_group()

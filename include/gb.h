@@ -167,8 +167,8 @@ int gb_set_config(gb_ctx* ctx, const gb_config* cfg);
 /* Autotuner (segment length, sieve tile, CTA size, tile / large-prime split, P):
  * verifies the sample workload [lo[i], hi[i]) i < count under candidate
  * settings, one parameter at a time (coordinate descent over tile_bits,
- * bucket_split, p1, cover_prefix and, for GB_TUNE_PLAIN, seg_len and
- * cta_threads), each timed with CUDA events on the context's stream as the
+ * bucket_split, p1, cover_prefix, cta_threads and, for GB_TUNE_PLAIN,
+ * seg_len), each timed with CUDA events on the context's stream as the
  * best of reps runs after a warm-up run; keeps the fastest setting in the
  * context and returns it in *out (optional) with its time in *best_ms
  * (optional).  mode GB_TUNE_PLAIN times gb_verify_range on each range,
@@ -299,8 +299,12 @@ int gb_partitions(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t* counts);
  *   - final bound max(P, p2) at most GB_NOALLOC_MAX_P;
  *   - seg_hist_stride at most GB_NOALLOC_MAX_STRIDE;
  *   - out->pmin, if given, must be device memory (GB_EINVAL otherwise).
+ * The large sieving primes always take the kernels that strike in place,
+ * whatever GB_LARGE asks for (the bucket lists are arenas sized on use).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture, and do not keep using the library
+ * across a cudaDeviceReset of that device (the kept address would be stale).
  * All calls share the one array: each clears what must start at zero, and
  * calls whose work overlaps on the GPU (other streams, other threads) race. */
 #define GB_NOALLOC_SCRATCH_BYTES (4u << 20)
@@ -334,6 +338,19 @@ int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterat
 /* Kernels launched by verification calls of this context since the last
  * gb_profile_enable (counted whether or not profiling is on). */
 int gb_profile_kernels(gb_ctx* ctx, uint64_t* kernels);
+
+/* Bytes copied between host and device memory by the calls of this context
+ * since the last gb_profile_enable (every cudaMemcpyAsync the library issues
+ * for the caller: inputs and staged descriptors to the device, results and
+ * the counters the host reads back to the host; counted whether or not
+ * profiling is on).  Either pointer may be NULL. */
+int gb_profile_copies(gb_ctx* ctx, uint64_t* h2d_bytes, uint64_t* d2h_bytes);
+
+/* Device (cudaMalloc) and pinned host (cudaMallocHost) allocations the
+ * library has made in this process so far, and their total bytes: a call
+ * allocated nothing iff the count is the same before and after it.  Either
+ * pointer may be NULL. */
+void gb_alloc_stats(uint64_t* count, uint64_t* bytes);
 
 /* Bytes of the odd-only dense bitset for the odd numbers 3..N (Sec. 2.2):
  * ceil(#odd in [3, N] / 64) 64-bit words.  Host-only helper. */

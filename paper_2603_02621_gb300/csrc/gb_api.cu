@@ -15,6 +15,7 @@
 #include "gb_runtime.cuh"
 
 thread_local std::string g_last_error;
+std::atomic<uint64_t> g_alloc_count{0}, g_alloc_bytes{0};
 
 int fail(int code, const std::string& msg)
 {
@@ -72,7 +73,7 @@ int tile_sieve_args(gb_ctx* ctx, int64_t B, uint64_t nbits, gb::SieveArgs& a, ui
     return GB_OK;
 }
 
-int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned long long* popc)
+int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned long long* popc, bool may_alloc)
 {
     if (nbits == 0) return GB_OK;
     // primes from bucket_split on are struck by the large-prime kernel, chunk
@@ -115,7 +116,9 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
         // primes of at least a bucket tile (2^20) go to the bucket sieve; those
         // between the split and a bucket tile hit a tile several times and
         // keep the atomic kernel
-        const uint64_t nbucket_lo = ctx->bucket_large ? std::max<uint64_t>(nmid, ctx->pi((1u << gb::kBucketTileLog2) - 1)) : np;
+        // (never for a caller that must not allocate: the lists are sized on use)
+        const uint64_t nbucket_lo = ctx->bucket_large && may_alloc
+                                        ? std::max<uint64_t>(nmid, ctx->pi((1u << gb::kBucketTileLog2) - 1)) : np;
         if (nbucket_lo < np) {
             // bucket sieve, chunk by chunk of at most 2^30 bits; a chunk whose
             // lists overflowed is struck again by the atomic kernel below
@@ -147,7 +150,7 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
                 GB_LAUNCH(gb::launch_bucket_apply(aa, ctx->stream));
             }
             std::vector<unsigned int> flags(nchunks);
-            GB_CUDA(cudaMemcpyAsync(flags.data(), ctx->bflags.p, nchunks * 4, cudaMemcpyDeviceToHost, ctx->stream));
+            GB_CUDA(ctx->copy(flags.data(), ctx->bflags.p, nchunks * 4, cudaMemcpyDeviceToHost, ctx->stream));
             GB_CUDA(cudaStreamSynchronize(ctx->stream));
             for (uint32_t c = 0; c < nchunks; ++c) {
                 if (!flags[c]) continue;
@@ -195,12 +198,12 @@ int build_primes(gb_ctx* ctx)
                        seedr.as<uint64_t>()};
     GB_CUDA(gb::launch_compact(ca, s));
     std::vector<uint32_t> seedw(seed_words);
-    GB_CUDA(cudaMemcpyAsync(seedw.data(), seedbits.p, seed_words * 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(ctx->copy(seedw.data(), seedbits.p, seed_words * 4, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     size_t nseed = 1;                                 // the prime 2
     for (uint32_t v : seedw) nseed += (size_t)__builtin_popcount(v);
     std::vector<uint32_t> seed(nseed);
-    GB_CUDA(cudaMemcpyAsync(seed.data(), seedp.p, nseed * 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(ctx->copy(seed.data(), seedp.p, nseed * 4, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     seedbits.release();
 
@@ -228,7 +231,7 @@ int build_primes(gb_ctx* ctx)
     GB_CUDA(cudaMemsetAsync(popc.p, 0, 8, s));
     if ((rc = run_sieve(ctx, 1, nbits, bits.as<uint32_t>(), popc.as<unsigned long long>()))) return rc;
     unsigned long long nodd = 0;
-    GB_CUDA(cudaMemcpyAsync(&nodd, popc.p, 8, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(ctx->copy(&nodd, popc.p, 8, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     const uint64_t n = nodd + 1;
     DevBuf np, nr;
@@ -236,7 +239,7 @@ int build_primes(gb_ctx* ctx)
     gb::CompactArgs cb{bits.as<uint32_t>(), nwords, 1, counts.as<uint32_t>(), np.as<uint32_t>(), nr.as<uint64_t>()};
     GB_CUDA(gb::launch_compact(cb, s));
     ctx->base->h_primes.resize(n);
-    GB_CUDA(cudaMemcpyAsync(ctx->base->h_primes.data(), np.p, n * 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(ctx->copy(ctx->base->h_primes.data(), np.p, n * 4, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     ctx->base->primes.take(np);
     ctx->base->recip.take(nr);
@@ -277,7 +280,10 @@ int ctx_view(const gb_ctx* ctx, CtxView* v)
     return GB_OK;
 }
 uint64_t ctx_pi(const gb_ctx* ctx, uint64_t x) { return ctx->pi(x); }
-int ctx_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out) { return run_sieve(ctx, B, nbits, out, nullptr); }
+int ctx_sieve_noalloc(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out)
+{
+    return run_sieve(ctx, B, nbits, out, nullptr, false);
+}
 int set_error(int code, const char* msg) { return fail(code, msg); }
 }  // namespace gb
 
@@ -434,7 +440,7 @@ int gb_sieve_segment(gb_ctx* ctx, int64_t A_odd, uint64_t n_bits, uint64_t* q_bi
                    ctx->counter.as<unsigned long long>());
     if (rc) return rc;
     unsigned long long c = 0;
-    GB_CUDA(cudaMemcpyAsync(&c, ctx->counter.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(ctx->copy(&c, ctx->counter.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
     if (popcount) *popcount = c;
     return GB_OK;
@@ -462,7 +468,7 @@ int gb_prime_pi(gb_ctx* ctx, uint64_t x, uint64_t* count)
         if (rc) return rc;
     }
     unsigned long long c = 0;
-    GB_CUDA(cudaMemcpyAsync(&c, ctx->counter.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(ctx->copy(&c, ctx->counter.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
     *count = c + 1;                                 // + the prime 2
     return GB_OK;
@@ -477,6 +483,7 @@ int gb_profile_enable(gb_ctx* ctx, int enable)
     for (int k = 0; k < GB_PROF_KINDS; ++k) { ctx->prof_ms[k] = 0; ctx->prof_launches[k] = 0; ctx->prof_units[k] = 0; }
     ctx->work_strikes = ctx->work_iters = ctx->work_large = 0;
     ctx->kernels = 0;
+    ctx->copied_h2d = ctx->copied_d2h = 0;
     if (enable && !ctx->work.p) {
         if ((rc = ctx->work.ensure(24))) return rc;
         GB_CUDA(cudaMemset(ctx->work.p, 0, 24));
@@ -504,6 +511,20 @@ int gb_profile_kernels(gb_ctx* ctx, uint64_t* kernels)
     if (!ctx || !kernels) return fail(GB_EINVAL, "NULL argument");
     *kernels = ctx->kernels;
     return GB_OK;
+}
+
+int gb_profile_copies(gb_ctx* ctx, uint64_t* h2d_bytes, uint64_t* d2h_bytes)
+{
+    if (!ctx) return fail(GB_EINVAL, "NULL argument");
+    if (h2d_bytes) *h2d_bytes = ctx->copied_h2d;
+    if (d2h_bytes) *d2h_bytes = ctx->copied_d2h;
+    return GB_OK;
+}
+
+void gb_alloc_stats(uint64_t* count, uint64_t* bytes)
+{
+    if (count) *count = g_alloc_count.load();
+    if (bytes) *bytes = g_alloc_bytes.load();
 }
 
 int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterations, uint64_t* large_strikes)

@@ -156,7 +156,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     }
     unsigned char* dd = static_cast<unsigned char*>(ctx->bdesc.p);
     const size_t used = reinterpret_cast<unsigned char*>(counts + 5) - hs_p;
-    GB_CUDA(cudaMemcpyAsync(dd, hs_p, used, cudaMemcpyHostToDevice, s));
+    GB_CUDA(ctx->copy(dd, hs_p, used, cudaMemcpyHostToDevice, s));
     const gb::BatchRange* d_ranges = reinterpret_cast<const gb::BatchRange*>(dd);
     const gb::LargePiece* d_pieces = reinterpret_cast<const gb::LargePiece*>(dd + (size_t)count * sizeof(gb::BatchRange));
     const uint32_t* d_s_range = reinterpret_cast<const uint32_t*>(dd + desc_ranges);
@@ -318,9 +318,9 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
 
     // results to the caller; ranges with open n are redone with the retry pass
     std::vector<gb::SegRecord> rec(count);
-    GB_CUDA(cudaMemcpyAsync(rec.data(), d_records, (size_t)count * sizeof(gb::SegRecord), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(ctx->copy(rec.data(), d_records, (size_t)count * sizeof(gb::SegRecord), cudaMemcpyDeviceToHost, s));
     if (want_rows && !rows_dev)
-        GB_CUDA(cudaMemcpyAsync(hist, ctx->brows.p, (size_t)count * hist_stride * 8, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(ctx->copy(hist, ctx->brows.p, (size_t)count * hist_stride * 8, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     int status = GB_OK;
     for (uint32_t i = 0; i < count; ++i) {
@@ -340,14 +340,15 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
             r.max_pmin_n = one.max_pmin_n;
             r.hist_len = one.hist_len;
             if (res_dev)
-                GB_CUDA(cudaMemcpy(reinterpret_cast<gb::SegRecord*>(results) + i, &r, sizeof r, cudaMemcpyHostToDevice));
+                GB_CUDA(ctx->copy(reinterpret_cast<gb::SegRecord*>(results) + i, &r, sizeof r, cudaMemcpyHostToDevice, s));
             if (want_rows) {
                 if (rows_dev)
-                    GB_CUDA(cudaMemcpy(hist + (uint64_t)i * hist_stride, row.data(), (size_t)hist_stride * 8,
-                                       cudaMemcpyHostToDevice));
+                    GB_CUDA(ctx->copy(hist + (uint64_t)i * hist_stride, row.data(), (size_t)hist_stride * 8,
+                                      cudaMemcpyHostToDevice, s));
                 else
                     std::memcpy(hist + (uint64_t)i * hist_stride, row.data(), (size_t)hist_stride * 8);
             }
+            if (res_dev || (want_rows && rows_dev)) GB_CUDA(cudaStreamSynchronize(s));   // r and row are reused
         }
         if (want_rows && r.hist_len > hist_stride) status = GB_ERANGE;
     }

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(128) k_retry(const RetryArgs a)
 
 cudaError_t launch_retry(const RetryArgs& a, cudaStream_t s)
 {
-    k_retry<<<2 * 152, 128, 0, s>>>(a);
+    k_retry<<<2 * device_sms(), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

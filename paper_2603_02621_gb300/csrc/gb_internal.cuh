@@ -28,6 +28,11 @@ constexpr uint32_t kWheelWords = kWheelW1 + kWheelW2 + kWheelW3 + kWheelW4;   //
 constexpr uint32_t kStampedPrimes = 14u;    // 3 .. 43 come from the stamp
 constexpr uint32_t kFirstStrikeIdx = 14u;   // index of 47 in 2,3,5,7,...,43,47,...
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// looked up once per device ordinal); grids of persistent or grid-stride
+// kernels are sized as multiples of it.  1 if the query fails.
+uint32_t device_sms();
+
 // Barrett reduction (P. Barrett, CRYPTO '86): with m = floor((2^64-1)/p), the
 // quotient estimate hi64(x*m) is at most 2 below floor(x/p); two conditional
 // subtractions finish the remainder.  p < 2^32, any 64-bit x.
@@ -408,8 +413,10 @@ struct CtxView {
 };
 int ctx_view(const gb_ctx* ctx, CtxView* v);
 uint64_t ctx_pi(const gb_ctx* ctx, uint64_t x);            // primes <= x (x <= L)
-// segment sieve of the odd numbers B + 2i, i < nbits, into out (device words)
-int ctx_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out);
+// segment sieve of the odd numbers B + 2i, i < nbits, into out (device
+// words), with no device allocation: the large primes take the kernels that
+// strike in place (never the bucket lists, which are sized on first use)
+int ctx_sieve_noalloc(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out);
 int set_error(int code, const char* msg);                 // records gb_last_error()
 
 }  // namespace gb

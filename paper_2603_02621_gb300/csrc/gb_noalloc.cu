@@ -157,7 +157,7 @@ extern "C" int gb_verify_range_noalloc(gb_ctx* ctx, uint64_t lo, uint64_t hi, ui
 
     // q window and cover: the same kernels and the same choices as gb_verify_range
     const int64_t B = (int64_t)lo - (int64_t)H + 1;
-    if ((rc = gb::ctx_sieve(ctx, B, qw * 64, reinterpret_cast<uint32_t*>(Q)))) return rc;
+    if ((rc = gb::ctx_sieve_noalloc(ctx, B, qw * 64, reinterpret_cast<uint32_t*>(Q)))) return rc;
     gb::CoverArgs ca{};
     ca.Q = Q;
     ca.H = H;

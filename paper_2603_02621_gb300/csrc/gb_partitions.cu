@@ -61,7 +61,8 @@ cudaError_t launch_reverse_bits(const uint32_t* P, uint32_t* rev, uint64_t words
 {
     if (!P || !rev) return cudaErrorInvalidValue;
     const uint64_t blocks = (words + 1 + 255) / 256;
-    k_reverse_bits<<<(unsigned)(blocks < 152ull * 32 ? blocks : 152ull * 32), 256, 0, s>>>(P, rev, words);
+    const uint64_t cap = (uint64_t)device_sms() * 32;
+    k_reverse_bits<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(P, rev, words);
     return cudaGetLastError();
 }
 

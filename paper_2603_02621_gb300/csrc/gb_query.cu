@@ -147,7 +147,8 @@ cudaError_t launch_query(const QueryArgs& a, cudaStream_t s)
 {
     if (a.count == 0) return cudaSuccess;
     if (!a.n || !a.primes || !a.recip || !a.out || !a.bad) return cudaErrorInvalidValue;
-    const uint32_t grid = a.count < 152u * 16 ? a.count : 152u * 16;
+    const uint32_t cap = device_sms() * 16u;
+    const uint32_t grid = a.count < cap ? a.count : cap;
     k_query<<<grid, kQueryThreads, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -25,7 +25,7 @@ int gb_query_batch(gb_ctx* ctx, const uint64_t* n, uint32_t count, uint32_t P, u
         return rc;
     const uint64_t* d_n = n;
     if (!n_dev) {
-        GB_CUDA(cudaMemcpyAsync(ctx->qn.p, n, (size_t)count * 8, cudaMemcpyHostToDevice, s));
+        GB_CUDA(ctx->copy(ctx->qn.p, n, (size_t)count * 8, cudaMemcpyHostToDevice, s));
         d_n = ctx->qn.as<uint64_t>();
     }
     unsigned int* bad = reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(ctx->qout.p) + (size_t)count * 4);
@@ -41,8 +41,8 @@ int gb_query_batch(gb_ctx* ctx, const uint64_t* n, uint32_t count, uint32_t P, u
     qa.bad = bad;
     GB_LAUNCH(gb::launch_query(qa, s));
     unsigned int h_bad = 0;
-    GB_CUDA(cudaMemcpyAsync(&h_bad, bad, 4, cudaMemcpyDeviceToHost, s));
-    if (!out_dev) GB_CUDA(cudaMemcpyAsync(p_min, qa.out, (size_t)count * 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(ctx->copy(&h_bad, bad, 4, cudaMemcpyDeviceToHost, s));
+    if (!out_dev) GB_CUDA(ctx->copy(p_min, qa.out, (size_t)count * 4, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     if (h_bad) return fail(GB_EINVAL, "n must be even, 4 <= n < 2^63 (device input)");
     return GB_OK;
@@ -83,7 +83,7 @@ int gb_partitions(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t* counts)
     const uint64_t need = ((hi - 4) / 2) / 2 / 32 + 1;                  // words of the largest n
     pa.runs = (need + pa.run_words - 1) / pa.run_words;
     GB_LAUNCH(gb::launch_partitions(pa, s));
-    if (!out_dev) GB_CUDA(cudaMemcpyAsync(counts, d_out, count * 4, cudaMemcpyDeviceToHost, s));
+    if (!out_dev) GB_CUDA(ctx->copy(counts, d_out, count * 4, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     return GB_OK;
 }

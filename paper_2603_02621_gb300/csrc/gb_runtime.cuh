@@ -5,6 +5,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -34,6 +35,9 @@ int fail(int code, const std::string& msg);
         ctx->kernels += 1;    \
     } while (0)
 
+// allocations made by the library in this process (gb_alloc_stats)
+extern std::atomic<uint64_t> g_alloc_count, g_alloc_bytes;
+
 struct DevBuf {
     void* p = nullptr;
     size_t cap = 0;
@@ -49,6 +53,8 @@ struct DevBuf {
             cudaGetLastError();
             return fail(GB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
+        g_alloc_count.fetch_add(1);
+        g_alloc_bytes.fetch_add(want);
         cap = want;
         return GB_OK;
     }
@@ -91,6 +97,8 @@ struct HostBuf {
             cudaGetLastError();
             return fail(GB_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
         }
+        g_alloc_count.fetch_add(1);
+        g_alloc_bytes.fetch_add(want);
         cap = want;
         return GB_OK;
     }
@@ -169,6 +177,15 @@ struct gb_ctx {
             return rc;
         GB_CUDA(cudaMemsetAsync(bflags.p, 0, (size_t)nchunks * 4, stream));
         return GB_OK;
+    }
+    // bytes copied between host and device memory by verification calls
+    // (gb_profile_copies), reset by gb_profile_enable
+    uint64_t copied_h2d = 0, copied_d2h = 0;
+    cudaError_t copy(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s)
+    {
+        if (kind == cudaMemcpyHostToDevice) copied_h2d += bytes;
+        else if (kind == cudaMemcpyDeviceToHost) copied_d2h += bytes;
+        return cudaMemcpyAsync(dst, src, bytes, kind, s);
     }
     bool capturing = false;           // cap_stream is being captured (profiling events become graph nodes)
     cudaStream_t cap_stream = nullptr;  // private stream the batch graph is captured on
@@ -270,8 +287,10 @@ int fill_defaults(gb_config& c);
 // of the last number and those below the split
 int tile_sieve_args(gb_ctx* ctx, int64_t B, uint64_t nbits, gb::SieveArgs& a, uint64_t& np, uint64_t& nsmall);
 // sieve of the window (B, nbits) into out (32-bit words; may be NULL when no
-// prime is above the split), popcount optional
-int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned long long* popc);
+// prime is above the split), popcount optional; may_alloc false keeps to the
+// kernels that need no buffer beyond out (no bucket lists)
+int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned long long* popc,
+              bool may_alloc = true);
 // base primes of a new context
 int build_primes(gb_ctx* ctx);
 // true for device (or managed) memory

@@ -15,10 +15,34 @@
 //     finished tile is stored with coalesced writes;
 //   * the first multiple of p in a tile comes from a Barrett remainder with a
 //     per-prime reciprocal, so no 64-bit division runs in the hot loop.
+#include <atomic>
+
 #include "gb_internal.cuh"
 #include "gb_sieve_tile.cuh"
 
 namespace gb {
+
+uint32_t device_sms()
+{
+    constexpr int kMaxDev = 64;
+    static std::atomic<uint32_t> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (dev >= 0 && dev < kMaxDev) {
+        const uint32_t c = cache[dev].load(std::memory_order_relaxed);
+        if (c) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (dev >= 0 && dev < kMaxDev) cache[dev].store((uint32_t)sms, std::memory_order_relaxed);
+    return (uint32_t)sms;
+}
 
 // ---------------------------------------------------------------------------
 // stamp tables: in table t, bit x (x = 0 .. 32*words-1) is 1 iff no prime of
@@ -120,20 +144,27 @@ __global__ void __launch_bounds__(NT) k_sieve_items(const SieveItemsArgs a)
     }
 }
 
-cudaError_t launch_sieve_items(const SieveItemsArgs& a, int threads, cudaStream_t s)
+template <int NT>
+static cudaError_t launch_sieve_items_nt(const SieveItemsArgs& a, cudaStream_t s)
 {
-    (void)threads;
-    constexpr int NT = 256;
     const size_t smem = (kWheelWords + 3) * 4 + (size_t)a.base.tile_bits / 8;
     auto k = k_sieve_items<NT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem)) != cudaSuccess) return e;
-    k<<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), NT, smem, s>>>(a);
+    k<<<(unsigned)(device_sms() * (per_sm > 0 ? per_sm : 1)), NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// persistent grid: as many CTAs of `threads` (128, 256 or 512) as fit on the device
+cudaError_t launch_sieve_items(const SieveItemsArgs& a, int threads, cudaStream_t s)
+{
+    switch (threads) {
+    case 128: return launch_sieve_items_nt<128>(a, s);
+    case 512: return launch_sieve_items_nt<512>(a, s);
+    default: return launch_sieve_items_nt<256>(a, s);
+    }
 }
 
 cudaError_t launch_sieve(const SieveArgs& a, int threads, cudaStream_t s)
@@ -207,7 +238,8 @@ __global__ void __launch_bounds__(256) k_large(const LargeArgs a)
 cudaError_t launch_large(const LargeArgs& a, cudaStream_t s)
 {
     if (a.n_primes == 0 || a.bit_hi <= a.bit_lo) return cudaSuccess;
-    const uint32_t grid = (a.n_primes + 255) / 256 < 152u * 64 ? (a.n_primes + 255) / 256 : 152u * 64;
+    const uint32_t cap = device_sms() * 64u;
+    const uint32_t grid = (a.n_primes + 255) / 256 < cap ? (a.n_primes + 255) / 256 : cap;
     k_large<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -324,7 +356,8 @@ cudaError_t launch_popcount(const uint32_t* words, uint64_t n, unsigned long lon
 {
     if (n == 0) return cudaSuccess;
     const uint64_t blocks = (n + 255) / 256;
-    k_popcount<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(words, n, count);
+    const uint64_t cap = (uint64_t)device_sms() * 16;
+    k_popcount<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(words, n, count);
     return cudaGetLastError();
 }
 

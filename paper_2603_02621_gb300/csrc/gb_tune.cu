@@ -140,11 +140,12 @@ extern "C" int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, 
                               c.seg_len = v;
                               return true;
                           }});
-        params.push_back({{128, 256, 512}, [](gb_config& c, uint32_t v) {
-                              c.cta_threads = v;
-                              return true;
-                          }});
     }
+    // the tile sieve's CTA size (plain and persistent batched launches alike)
+    params.push_back({{128, 256, 512}, [](gb_config& c, uint32_t v) {
+                          c.cta_threads = v;
+                          return true;
+                      }});
 
     for (const Param& p : params) {
         for (uint32_t v : p.values) {

@@ -145,7 +145,7 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
             // the retry pass reads Q from global memory: sieve the slab there
             // only if some word was left open
             unsigned int cnt = 0;
-            GB_CUDA(cudaMemcpyAsync(&cnt, ctx->retry_count.p, 4, cudaMemcpyDeviceToHost, s));
+            GB_CUDA(ctx->copy(&cnt, ctx->retry_count.p, 4, cudaMemcpyDeviceToHost, s));
             GB_CUDA(cudaStreamSynchronize(s));
             if (cnt) {
                 if ((rc = run_sieve(ctx, B, qw * 64, ctx->q.as<uint32_t>(), nullptr))) return rc;
@@ -192,12 +192,12 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
 
         if (retry) {
             unsigned int cnt = 0;
-            GB_CUDA(cudaMemcpyAsync(&cnt, ctx->retry_count.p, 4, cudaMemcpyDeviceToHost, s));
+            GB_CUDA(ctx->copy(&cnt, ctx->retry_count.p, 4, cudaMemcpyDeviceToHost, s));
             GB_CUDA(cudaStreamSynchronize(s));
             if (cnt > retry_cap) overflow_total += cnt - retry_cap;
         }
         if (out->pmin && !pmin_dev)
-            GB_CUDA(cudaMemcpyAsync(out->pmin + s0 * S, pm, n_count * 4, cudaMemcpyDeviceToHost, s));
+            GB_CUDA(ctx->copy(out->pmin + s0 * S, pm, n_count * 4, cudaMemcpyDeviceToHost, s));
     }
     if (overflow_total) {
         // the retry list could not hold every word left open: redo in one pass to Pf
@@ -227,14 +227,14 @@ int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_
     ctx->prof_end();
 
     gb::RangeTotals tot{};
-    GB_CUDA(cudaMemcpyAsync(&tot, ctx->totals.p, sizeof tot, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(ctx->copy(&tot, ctx->totals.p, sizeof tot, cudaMemcpyDeviceToHost, s));
     const uint32_t nh = out->hist ? std::min<uint32_t>(out->hist_cap, hist_stride) : 0;
-    if (nh) GB_CUDA(cudaMemcpyAsync(out->hist, ctx->merged.p, (size_t)nh * 8, cudaMemcpyDeviceToHost, s));
+    if (nh) GB_CUDA(ctx->copy(out->hist, ctx->merged.p, (size_t)nh * 8, cudaMemcpyDeviceToHost, s));
     const uint64_t nrec = out->segs ? std::min<uint64_t>(out->seg_cap, nseg) : 0;
     if (nrec && !segs_dev)
-        GB_CUDA(cudaMemcpyAsync(out->segs, ctx->records.p, nrec * sizeof(gb::SegRecord), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(ctx->copy(out->segs, ctx->records.p, nrec * sizeof(gb::SegRecord), cudaMemcpyDeviceToHost, s));
     if (rows_n && !rows_dev)
-        GB_CUDA(cudaMemcpyAsync(out->seg_hist, ctx->rows.p, rows_n * row_stride * 8, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(ctx->copy(out->seg_hist, ctx->rows.p, rows_n * row_stride * 8, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     if (out->hist) for (uint32_t i = nh; i < out->hist_cap; ++i) out->hist[i] = 0;
 

@@ -92,6 +92,8 @@ SIGNATURES = {
     "gb_profile_read": (c_int, [c_void_p, POINTER(ctypes.c_double), POINTER(c_uint64), POINTER(c_uint64)]),
     "gb_profile_work": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), POINTER(c_uint64)]),
     "gb_profile_kernels": (c_int, [c_void_p, POINTER(c_uint64)]),
+    "gb_profile_copies": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64)]),
+    "gb_alloc_stats": (None, [POINTER(c_uint64), POINTER(c_uint64)]),
     "gb_bitset_bytes": (c_uint64, [c_uint64]),
     "gb_strerror": (c_char_p, [c_int]),
     "gb_last_error": (c_char_p, []),
@@ -337,6 +339,21 @@ def gb_profile_kernels(ctx: int) -> int:
     n = c_uint64()
     _check(load().gb_profile_kernels(ctx, ctypes.byref(n)), "gb_profile_kernels")
     return n.value
+
+
+def gb_profile_copies(ctx: int) -> dict:
+    """Bytes the context's calls copied host -> device and device -> host
+    since the last gb_profile_enable."""
+    a, b = c_uint64(), c_uint64()
+    _check(load().gb_profile_copies(ctx, ctypes.byref(a), ctypes.byref(b)), "gb_profile_copies")
+    return dict(h2d=a.value, d2h=b.value)
+
+
+def gb_alloc_stats() -> dict:
+    """Device and pinned host allocations the library has made in this process."""
+    a, b = c_uint64(), c_uint64()
+    load().gb_alloc_stats(ctypes.byref(a), ctypes.byref(b))
+    return dict(count=a.value, bytes=b.value)
 
 
 def gb_verify_batch(ctx: int, ranges, P: int = 0, *, hist_stride: int = 0, results=None, hist=None,

@@ -118,18 +118,24 @@ def test_batch_rejects_bad_input(ctx, gbm):
 
 def test_batch_4096_ranges_sampled(ctx, oracle):
     """The 4096-range workload (lengths log-uniform 2^10..2^26 even n, starts
-    uniform in [1e9, 1e15]): invariants on every range, the oracle in full on
-    a seeded sample of the shorter ranges."""
+    uniform in [1e9, 1e15]): invariants on every range; 64 seeded ranges,
+    drawn from the whole batch (so from the whole length span), recomputed by
+    the oracle: records and p_min histogram rows element by element."""
     from paper_2603_02621_gb300.workloads import batched_ranges, sample_indices
     ranges = batched_ranges(count=4096, seed=1)
-    out = ctx.verify_batch(ranges)
+    stride = len(oracle.primes_upto(P1))
+    out = ctx.verify_batch(ranges, hist_stride=stride)
     for (lo, hi), r in zip(ranges, out["records"]):
         assert (r["lo"], r["hi"], r["n_checked"], r["unresolved"]) == (lo, hi, (hi - lo) // 2, 0)
         assert lo <= r["max_pmin_n"] < hi
         assert oracle.mr_isprime(r["max_pmin"]) and oracle.mr_isprime(r["max_pmin_n"] - r["max_pmin"])
-    short = [i for i, (lo, hi) in enumerate(ranges) if (hi - lo) // 2 <= (1 << 18)]
-    pick = [short[k] for k in sample_indices(len(short), 12, seed=3)]
-    _check_vs_oracle(oracle, [ranges[i] for i in pick], {"records": [out["records"][i] for i in pick]}, 0)
+    np.testing.assert_array_equal(out["hist"].sum(axis=1, dtype=np.uint64),
+                                  np.array([(hi - lo) // 2 for lo, hi in ranges], dtype=np.uint64))
+    pick = sample_indices(len(ranges), 64, seed=3)
+    lens = sorted((ranges[i][1] - ranges[i][0]) // 2 for i in pick)
+    assert lens[0] < (1 << 12) and lens[-1] > (1 << 24)          # the sample spans the length range
+    _check_vs_oracle(oracle, [ranges[i] for i in pick],
+                     {"records": [out["records"][i] for i in pick], "hist": out["hist"][pick]}, stride)
 
 
 def test_set_config_and_autotune(gbm):

@@ -43,6 +43,24 @@ def hist_len_for(oracle, P):
     return len(oracle.primes_upto(P))
 
 
+_ORACLE_SEGMENTS = {}
+
+
+def oracle_segments(oracle, lo, hi, S, P, HL):
+    """The oracle's per-segment records and histograms of [lo, hi), computed
+    once per module run and shared by the tests that compare with them."""
+    key = (lo, hi, S, P, HL)
+    if key not in _ORACLE_SEGMENTS:
+        _ORACLE_SEGMENTS[key] = oracle.verify_segments(lo, hi, S, P, HL, threads=oracle.default_threads())
+    return _ORACLE_SEGMENTS[key]
+
+
+def assert_segments_equal_oracle(r, summ, hist):
+    rec = [[s["n_checked"], s["unresolved"], s["max_pmin"], s["max_pmin_n"]] for s in r["segs"]]
+    assert rec == summ.tolist()
+    np.testing.assert_array_equal(r["seg_hist"], hist)
+
+
 # ------------------------------------------------------------------ sieve
 
 @pytest.mark.parametrize("A,nbits", [
@@ -201,11 +219,12 @@ def test_two_phase_without_retry_counts_unresolved(gbm, oracle):
 
 @pytest.mark.parametrize("ka", ["48", "64", "80", "144", "192", "256"])
 @pytest.mark.parametrize("lo", [10**6, 3 * 10**11, 4 * 10**18 - 10**7])
-def test_two_phase_matches_generic(gbm, monkeypatch, ka, lo):
+def test_two_phase_matches_generic(gbm, oracle, monkeypatch, ka, lo):
     """The block cover (a first block of 48 or 64 primes and 0 to 6 blocks of
     32, so the segment maximum comes from the probing or from a re-run of the
-    last block that set a bit, with its input list kept or overwritten) and the
-    generic cover kernel give identical results."""
+    last block that set a bit, with its input list kept or overwritten), the
+    generic cover kernel and the oracle give identical per-segment records
+    and histograms."""
     hi = lo + 2 * 5 * 10**6
     base = dict(device=0, base_limit=1 << 31, seg_len=1 << 20, p1=1 << 15, p2=1 << 20)
     monkeypatch.setenv("GB_KA", ka)
@@ -217,6 +236,35 @@ def test_two_phase_matches_generic(gbm, monkeypatch, ka, lo):
         b = g.verify_range(lo, hi, seg_hist_stride=3512, hist_cap=3512)
     assert a["segs"] == b["segs"]
     assert np.array_equal(a["seg_hist"], b["seg_hist"])
+    summ, hist = oracle_segments(oracle, lo, hi, 1 << 20, 1 << 20, 3512)
+    assert_segments_equal_oracle(a, summ, hist)
+
+
+@pytest.mark.parametrize("p2", [0, 1 << 20])
+def test_block_cover_48_schedule_chosen_by_magnitude(gbm, oracle, monkeypatch, p2):
+    """P1 = 293 holds 61 odd primes: near 1e12 the block cover is chosen
+    without an override and takes its 48-prime schedule (K in [48, 63]);
+    identical to the generic cover and to the oracle, with and without the
+    retry pass."""
+    monkeypatch.delenv("GB_KA", raising=False)
+    monkeypatch.delenv("GB_COVER", raising=False)
+    lo, hi = 10**12, 10**12 + 2 * 3 * 10**6
+    HL = 62                                        # primes <= 293
+    stride = HL if p2 == 0 else hist_len_for(oracle, p2)
+    base = dict(device=0, base_limit=1 << 20, seg_len=1 << 20, p1=293, p2=p2)
+    with gbm.Context(**base) as g:
+        a = g.verify_range(lo, hi, seg_hist_stride=stride, hist_cap=stride)
+    monkeypatch.setenv("GB_COVER", "generic")
+    with gbm.Context(**base) as g:
+        b = g.verify_range(lo, hi, seg_hist_stride=stride, hist_cap=stride)
+    assert a["segs"] == b["segs"]
+    assert np.array_equal(a["seg_hist"], b["seg_hist"])
+    summ, hist = oracle.verify_segments(lo, hi, 1 << 20, p2 or 293, stride, threads=oracle.default_threads())
+    assert_segments_equal_oracle(a, summ, hist)
+    if p2 == 0:
+        assert a["unresolved"] > 0
+    else:
+        assert a["unresolved"] == 0
 
 
 @pytest.mark.parametrize("p1,ka", [(420, "80"), (227, "48"), (313, "64"), (617, "112")])

@@ -3,9 +3,9 @@ paper's Table 4) and the 10^11-wide window below 4e18, segments of 2^27 even
 n, base primes to 2^31, P1 = 2^15 then the retry pass to P2 = 2^20.
 
 Every segment's record and histogram row is checked against invariants and
-the merged totals; a seeded sample of segments (GB_SAMPLED_SEGMENTS, default
-32; 256 for the full check) is recomputed by the CPU oracle and must match
-bit for bit."""
+the merged totals; a seeded sample of 256 segments per range
+(GB_SAMPLED_SEGMENTS to change it) is recomputed by the CPU oracle and must
+match bit for bit."""
 import concurrent.futures as cf
 import os
 
@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 S = 1 << 27
 P1, P2 = 1 << 15, 1 << 20
 HL = 3512                      # pi(2^15)
-SAMPLES = int(os.environ.get("GB_SAMPLED_SEGMENTS", "32"))
+SAMPLES = int(os.environ.get("GB_SAMPLED_SEGMENTS", "256"))
 
 
 @pytest.fixture(scope="module")
