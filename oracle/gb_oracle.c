@@ -396,6 +396,50 @@ uint64_t or_count_strikes(int64_t a_odd, uint64_t nbits, uint64_t p_lo, uint64_t
     return total;
 }
 
+/* number of odd t in [lo, hi] (0 if hi < lo) */
+static uint64_t odd_count(uint64_t lo, uint64_t hi)
+{
+    if (hi < lo) return 0;
+    const uint64_t first = lo | 1, last = (hi & 1) ? hi : hi - 1;
+    return last >= first ? (last - first) / 2 + 1 : 0;
+}
+
+/* number of odd multiples of the odd number d in [lo, hi] */
+static uint64_t odd_multiples(uint64_t lo, uint64_t hi, uint64_t d)
+{
+    if (hi < lo) return 0;
+    return odd_count((lo + d - 1) / d, hi / d);
+}
+
+/*
+ * Like or_count_strikes, counting only the multiples j*p with j coprime to 15
+ * (j odd): the strikes a sieve makes when the multiples of 3 and 5 are
+ * already cleared.  Per prime, by inclusion and exclusion over the odd j in
+ * [jlo, jhi]: all, minus those divisible by 3, minus those divisible by 5,
+ * plus those divisible by 15.
+ */
+uint64_t or_count_strikes_coprime15(int64_t a_odd, uint64_t nbits, uint64_t p_lo, uint64_t p_hi)
+{
+    if (nbits == 0) return 0;
+    const int64_t last = a_odd + 2 * (int64_t)(nbits - 1);
+    if (last < 4) return 0;
+    const uint64_t r = or_isqrt((uint64_t)last);
+    if (p_hi > r) p_hi = r;
+    if (ensure_small(p_hi < 16 ? 16 : p_hi)) return 0;
+    uint64_t total = 0;
+    for (uint64_t k = 0; k < g_nsmall && g_small[k] <= p_hi; k++) {
+        const uint64_t p = g_small[k];
+        if (p < p_lo || p == 2) continue;
+        uint64_t L = p * p;
+        if (a_odd > 0 && (uint64_t)a_odd > L) L = (uint64_t)a_odd;
+        const uint64_t jlo = (L + p - 1) / p, jhi = (uint64_t)last / p;
+        if (jhi < jlo) continue;
+        total += odd_multiples(jlo, jhi, 1) - odd_multiples(jlo, jhi, 3) - odd_multiples(jlo, jhi, 5) +
+                 odd_multiples(jlo, jhi, 15);
+    }
+    return total;
+}
+
 uint64_t or_partitions(uint64_t n)
 {
     if (n < 4 || (n & 1)) return 0;

@@ -79,6 +79,8 @@ def _load():
         lib.or_td_partitions.argtypes = [u64]
         lib.or_count_strikes.restype = u64
         lib.or_count_strikes.argtypes = [i64, u64, u64, u64]
+        lib.or_count_strikes_coprime15.restype = u64
+        lib.or_count_strikes_coprime15.argtypes = [i64, u64, u64, u64]
         lib.or_prime_pi.restype = u64
         lib.or_prime_pi.argtypes = [u64, ctypes.c_int]
         _lib = lib
@@ -175,6 +177,12 @@ def count_strikes(a_odd: int, nbits: int, p_lo: int, p_hi: int) -> int:
     """Strikes of the primes in [p_lo, p_hi] (from p^2 on) in the window of
     nbits odd numbers from a_odd."""
     return int(_load().or_count_strikes(a_odd, nbits, p_lo, p_hi))
+
+
+def count_strikes_coprime15(a_odd: int, nbits: int, p_lo: int, p_hi: int) -> int:
+    """As count_strikes, only the multiples j p with j coprime to 15 (the
+    strikes left when the multiples of 3 and 5 are cleared already)."""
+    return int(_load().or_count_strikes_coprime15(a_odd, nbits, p_lo, p_hi))
 
 
 def cover_iterations(lo: int, hi: int, P: int) -> int:

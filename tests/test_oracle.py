@@ -248,6 +248,31 @@ def test_strike_count_brute_force(oracle, a, nbits, plo, phi):
     assert oracle.count_strikes(a, nbits, plo, phi) == want
 
 
+@pytest.mark.parametrize("a,nbits,plo,phi", [
+    (1, 5000, 3, 10**6),
+    (10**6 + 1, 3001, 47, 10**6),
+    (10**9 + 7, 999, 5, 31),
+    (-41, 300, 3, 100),
+    (10**12 + 1, 4001, 7, 10**6),
+])
+def test_strike_count_coprime15_brute_force(oracle, a, nbits, plo, phi):
+    # every odd number m = j p of the window, p in range, m >= p^2, with the
+    # cofactor j coprime to 15
+    last = a + 2 * (nbits - 1)
+    primes = [p for p in oracle.primes_upto(min(phi, math.isqrt(max(last, 0)))).tolist() if p >= plo and p > 2]
+    want = 0
+    for i in range(nbits):
+        m = a + 2 * i
+        if m < 4:
+            continue
+        want += sum(1 for p in primes if m % p == 0 and m >= p * p and math.gcd(m // p, 15) == 1)
+    got = oracle.count_strikes_coprime15(a, nbits, plo, phi)
+    assert got == want
+    # the cofactors divisible by 3 or 5 are exactly the rest
+    if plo > 5:
+        assert got < oracle.count_strikes(a, nbits, plo, phi) or want == 0
+
+
 def test_cover_iterations_worked_by_hand(oracle):
     # one 64-n word, n = 4 .. 130: the largest p_min there is 19 (at n = 98
     # and n = 128: n - 3, ..., n - 17 are all composite, n - 19 is prime),
