@@ -58,7 +58,8 @@ PLAIN_MODES = {
 # DRAM bytes per unit (even n) of the dominant kernels, from ncu captures
 # (profiles/): scaled to a launch by the units it processes
 NCU_TRAFFIC = {
-    "plain": {"cover": 0.1270, "sieve": 0.09678},
+    "plain": {"cover": 0.1270, "sieve": 0.09678},                 # [4, 2^32] (profiles/k_*_4_to_2e32.md)
+    "exhaustive-1e12": {"cover": 0.1270, "sieve": 0.09684},       # 2^31 n near 1e12 (profiles/k_*_1e12.md)
 }
 
 

@@ -46,6 +46,7 @@ extern "C" {
 #define GB_ETIMEOUT  4  /* a bounded device wait gave up */
 #define GB_EBUSY     5  /* the context is in use */
 #define GB_ERANGE    6  /* an output buffer is too small; everything that fit was written */
+#define GB_ECANCELED 7  /* a server request was cancelled before it ran */
 
 typedef struct gb_ctx gb_ctx;
 
@@ -177,6 +178,19 @@ int gb_set_config(gb_ctx* ctx, const gb_config* cfg);
 #define GB_TUNE_BATCH 1
 int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_t count, int mode, uint32_t reps,
                 gb_config* out, double* best_ms);
+/* Autotune cache.  When the environment variable GB_TUNE_CACHE names a file,
+ * gb_autotune first looks up the key "<GPU name>|<SM count>|<mode>|<count>|
+ * <hash of the sample's bounds>|<base_limit>|<p2>|<slab_bits>" there: on a
+ * hit it applies the stored setting without timing anything (best_ms is the
+ * stored time); otherwise it searches and appends one line
+ * "<key>\t<tile_bits> <bucket_split> <p1> <cover_prefix> <seg_len>
+ * <cta_threads> <best ms>".  The last line of a key wins; damaged lines are
+ * skipped.  Host-only helpers over that file format: lookup returns GB_OK and
+ * fills those fields of *cfg (the rest untouched), GB_ERANGE when the key is
+ * absent or the file cannot be read; store appends (GB_EINVAL if the file
+ * cannot be written or the key holds a tab or newline). */
+int gb_tune_cache_lookup(const char* path, const char* key, gb_config* cfg, double* best_ms);
+int gb_tune_cache_store(const char* path, const char* key, const gb_config* cfg, double best_ms);
 
 /* Sieve one window of odd numbers (Sec. 2.2 layout, Sec. 2.3.1 segment sieve):
  * bit i (bit i%64 of word i/64, little-endian bit order) of q_bits is 1 iff the
@@ -263,8 +277,14 @@ typedef struct gb_server gb_server;
 /* lanes (range lanes) 1..16; hbm_budget_bytes 0 = half of the device memory free at
  * creation (cudaMemGetInfo); max_batch 0 = 256 */
 int gb_server_create(gb_server** out, gb_ctx* ctx, uint32_t lanes, uint64_t hbm_budget_bytes, uint32_t max_batch);
-/* queue a request (GB_EINVAL if it is malformed or beyond base_limit^2) */
+/* queue a request (GB_EINVAL if it is malformed or beyond base_limit^2;
+ * GB_EBUSY if the server is stopping or refuses it at admission) */
 int gb_server_submit(gb_server* srv, const gb_request* req, uint64_t* ticket);
+/* cancel a request still waiting in its queue: its response carries status
+ * GB_ECANCELED and can be collected with gb_server_wait.  GB_EBUSY if it is
+ * no longer queued (taken by a lane, which runs it to the end, or finished),
+ * GB_EINVAL for a ticket that was never issued. */
+int gb_server_cancel(gb_server* srv, uint64_t ticket);
 /* wait for a ticket's response (each ticket can be collected once);
  * GB_ETIMEOUT if it is not done within timeout_ms */
 int gb_server_wait(gb_server* srv, uint64_t ticket, gb_response* out, uint32_t timeout_ms);
@@ -338,6 +358,38 @@ int gb_profile_work(gb_ctx* ctx, uint64_t* sieve_strikes, uint64_t* cover_iterat
 /* Kernels launched by verification calls of this context since the last
  * gb_profile_enable (counted whether or not profiling is on). */
 int gb_profile_kernels(gb_ctx* ctx, uint64_t* kernels);
+
+/* Debug builds (the library compiled with -DGB_DEBUG, libgb_debug.so): the
+ * kernels check their shared- and global-memory strikes and bucket writes
+ * against the bounds of their buffers; a failed check records its site
+ * (1 tile strike, 2 slice strike, 3 large-prime strike, 4 carried strike,
+ * 5 bucket entry) in a device word and skips the access instead of trapping.
+ * gb_debug_word returns the first recorded site, 0 if none (always 0 in a
+ * release build), and clears the words if reset is nonzero.  It synchronizes
+ * with the device.  gb_debug_build is 1 in a debug build, 0 otherwise. */
+uint32_t gb_debug_word(int reset);
+int gb_debug_build(void);
+
+/* Host-side fault injection, for tests of the error paths (the paper has no
+ * counterpart).  Every fault is made on the host, none on the GPU: spec
+ * "kind@n[,kind@n...]" makes the n-th event of that kind from now on fail,
+ * with kind
+ *   alloc   a device or pinned-host allocation of the library: the call that
+ *           needed it returns GB_ENOMEM without calling the allocator (the
+ *           context stays usable);
+ *   submit  gb_server_submit: refused at admission with GB_EBUSY;
+ *   cancel  gb_server_submit: the request is queued, then cancelled at once
+ *           as by gb_server_cancel (its response carries GB_ECANCELED).
+ * NULL or "" clears every fault.  The GB_FAULT environment variable, if set,
+ * is applied at the first gb_init of the process.  GB_EINVAL for a malformed
+ * spec (the faults in force do not change). */
+#define GB_FAULT_ALLOC  0
+#define GB_FAULT_SUBMIT 1
+#define GB_FAULT_CANCEL 2
+int gb_fault_set(const char* spec);
+/* count one event of the kind against the spec in force: 1 if it is the one
+ * that fails (the check the library makes at each allocation and submit) */
+int gb_fault_tick(int kind);
 
 /* Bytes copied between host and device memory by the calls of this context
  * since the last gb_profile_enable (every cudaMemcpyAsync the library issues

@@ -73,6 +73,61 @@ int tile_sieve_args(gb_ctx* ctx, int64_t B, uint64_t nbits, gb::SieveArgs& a, ui
     return GB_OK;
 }
 
+// The base primes [k0, k1) (from the slice limit on, every p^2 <= B) over the
+// window (B, nbits), struck chunk by chunk of 2^clog2 bits with each prime
+// started once and carried (gb_large.cu): the primes below half a chunk in
+// per-prime words, the larger ones in a ring of per-chunk buckets.  A bucket
+// holds at most the primes with a multiple m p (m coprime to 30) in one
+// chunk: C (8/15) sum 1/p, which Mertens' theorem puts at
+// C (8/15) (ln ln p_hi - ln ln p_lo); an entry that still finds its bucket
+// full is struck through to the window's end by the kernel itself.
+static int carry_large(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, uint64_t k0, uint64_t k1,
+                       uint32_t clog2)
+{
+    const uint64_t C = 1ull << clog2;
+    const uint64_t kd = std::min<uint64_t>(k1, std::max<uint64_t>(k0, ctx->pi(C / 2 - 1)));
+    gb::BucketLargeArgs a{};
+    a.B = B;
+    a.nbits = nbits;
+    a.chunk_log2 = clog2;
+    a.nchunks = (uint32_t)((nbits + C - 1) >> clog2);
+    a.B_mod30 = (uint32_t)(B % 30);
+    a.primes = ctx->base->primes.as<uint32_t>() + k0;
+    a.recip = ctx->base->recip.as<uint64_t>() + k0;
+    a.n_dense = (uint32_t)(kd - k0);
+    a.n_sparse = (uint32_t)(k1 - kd);
+    uint32_t R = 1;
+    a.grid = gb::carry_grid();
+    if (a.n_sparse) {
+        const double p_lo = (double)ctx->base->h_primes[kd], p_hi = (double)ctx->base->h_primes[k1 - 1];
+        // an entry moves at most 1 + 3 p / C chunks ahead; the bucket being
+        // drained and the one drained before it must stay out of reach
+        const uint64_t adv = 1 + ((3ull * ctx->base->h_primes[k1 - 1]) >> clog2);
+        while (R < adv + 2) R <<= 1;
+        if (R > gb::kCarryMaxRing) return fail(GB_EINVAL, "internal: carried primes reach too many chunks ahead");
+        // each CTA's column holds its share (1 / grid) of a bucket
+        const double M = (double)C * (8.0 / 15.0) * (std::log(std::log(p_hi)) - std::log(std::log(p_lo)) + 1.0 / p_lo) /
+                         a.grid;
+        a.cap = (uint32_t)std::min(2.0e9, 1.15 * M + 8.0 * std::sqrt(M) + 64.0);
+    }
+    const size_t ncnt = (size_t)R * a.grid;
+    int rc;
+    if ((a.n_dense && (rc = ctx->cstate.ensure((size_t)a.n_dense * 4))) ||
+        (a.n_sparse && (rc = ctx->cring.ensure(ncnt * a.cap * 8))) || (rc = ctx->ccnt.ensure((ncnt + 1) * 4)))
+        return rc;
+    a.dstate = ctx->cstate.as<uint32_t>();
+    a.ring = ctx->cring.as<uint64_t>();
+    a.ring_cnt = ctx->ccnt.as<uint32_t>();
+    a.ring_mask = R - 1;
+    a.spills = ctx->ccnt.as<unsigned int>() + ncnt;
+    a.out = out;
+    a.strikes = ctx->work_ptr(2);
+    GB_CUDA(cudaMemsetAsync(ctx->ccnt.p, 0, (ncnt + 1) * 4, ctx->stream));
+    GB_LAUNCH(gb::launch_large_start(a, ctx->stream));
+    for (uint32_t c = 0; c < a.nchunks; ++c) GB_LAUNCH(gb::launch_large_chunk(a, c, ctx->stream));
+    return GB_OK;
+}
+
 int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned long long* popc, bool may_alloc)
 {
     if (nbits == 0) return GB_OK;
@@ -165,8 +220,22 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
                 GB_LAUNCH(gb::launch_large(lb, ctx->stream));
             }
         }
-        if (nbucket_lo > nmid) {
-            la.n_primes = (uint32_t)(nbucket_lo - nmid);
+        // the primes with p^2 <= B, over a window of two chunks or more: started
+        // once, carried from chunk to chunk; the rest restart in every chunk
+        uint64_t natomic = nmid;
+        const uint32_t clog2 = 28;
+        if (nbucket_lo > nmid && ctx->carry_large && may_alloc && B > 0 && (nbits >> clog2) >= 2) {
+            const uint64_t kb1 = std::min<uint64_t>(nbucket_lo, std::max<uint64_t>(nmid, ctx->pi(isqrt_u64((uint64_t)B))));
+            if (kb1 > nmid) {
+                int rc = carry_large(ctx, B, nbits, out, nmid, kb1, clog2);
+                if (rc) return rc;
+                natomic = kb1;
+            }
+        }
+        if (nbucket_lo > natomic) {
+            la.primes = ctx->base->primes.as<uint32_t>() + natomic;
+            la.recip = ctx->base->recip.as<uint64_t>() + natomic;
+            la.n_primes = (uint32_t)(nbucket_lo - natomic);
             const uint64_t chunk = ctx->large_chunk_bits;
             for (uint64_t c0 = 0; c0 < nbits; c0 += chunk) {
                 la.bit_lo = c0;
@@ -258,6 +327,19 @@ bool is_device_ptr(const void* p)
 
 // accessors for entry points in other translation units
 namespace gb {
+// readers of the debug words of the translation units built with GB_DEBUG
+// (registered while the library loads; a function-local list, so the order in
+// which the units initialise does not matter)
+static std::vector<uint32_t (*)(bool)>& debug_readers()
+{
+    static std::vector<uint32_t (*)(bool)> r;
+    return r;
+}
+int debug_register(uint32_t (*reader)(bool reset))
+{
+    debug_readers().push_back(reader);
+    return (int)debug_readers().size();
+}
 int ctx_view(const gb_ctx* ctx, CtxView* v)
 {
     if (!ctx || !v) return fail(GB_EINVAL, "NULL argument");
@@ -299,6 +381,7 @@ const char* gb_strerror(int code)
     case GB_ETIMEOUT: return "GB_ETIMEOUT: bounded device wait gave up";
     case GB_EBUSY: return "GB_EBUSY: context busy";
     case GB_ERANGE: return "GB_ERANGE: output buffer too small";
+    case GB_ECANCELED: return "GB_ECANCELED: request cancelled before it ran";
     default: return "unknown gb error";
     }
 }
@@ -316,6 +399,7 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
 {
     if (!out) return fail(GB_EINVAL, "out is NULL");
     *out = nullptr;
+    gb::fault_from_env();
     gb_config c{};
     if (cfg) c = *cfg;
     int rc = fill_defaults(c);
@@ -336,7 +420,10 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     if (const char* e = getenv("GB_WARP_SPLIT")) ctx->warp_split = atoi(e);
     if (const char* e = getenv("GB_COVER")) ctx->generic_cover = std::string(e) == "generic";
     if (const char* e = getenv("GB_BATCH_GRAPH")) ctx->batch_graph = atoi(e) != 0;
-    if (const char* e = getenv("GB_LARGE")) ctx->bucket_large = std::string(e) == "bucket";
+    if (const char* e = getenv("GB_LARGE")) {
+        ctx->bucket_large = std::string(e) == "bucket";
+        ctx->carry_large = std::string(e) != "atomic";
+    }
     if (const char* e = getenv("GB_FUSED")) ctx->fused = atoi(e) != 0;
     if (const char* e = getenv("GB_MID_LOG2")) {
         const int v = atoi(e);
@@ -377,6 +464,7 @@ int gb_init_shared(gb_ctx** out, const gb_ctx* parent, void* stream)
     ctx->batch_graph = parent->batch_graph;
     ctx->large_chunk_bits = parent->large_chunk_bits;
     ctx->bucket_large = parent->bucket_large;
+    ctx->carry_large = parent->carry_large;
     ctx->fused = parent->fused;
     ctx->mid_limit = parent->mid_limit;
     *out = ctx;
@@ -396,6 +484,7 @@ void gb_destroy(gb_ctx* ctx)
                       &ctx->rows, &ctx->merged, &ctx->pmin, &ctx->counter, &ctx->totals, &ctx->records, &ctx->work,
                       &ctx->bq, &ctx->bhist, &ctx->bkeys, &ctx->bunres, &ctx->bdesc, &ctx->brecords, &ctx->brows,
                       &ctx->qn, &ctx->qout, &ctx->blists, &ctx->bcounts, &ctx->bflags,
+                      &ctx->cstate, &ctx->cring, &ctx->ccnt,
                       &ctx->part_p, &ctx->part_rev, &ctx->part_out};
     for (DevBuf* b : bufs) b->release();
     delete ctx;
@@ -519,6 +608,25 @@ int gb_profile_copies(gb_ctx* ctx, uint64_t* h2d_bytes, uint64_t* d2h_bytes)
     if (h2d_bytes) *h2d_bytes = ctx->copied_h2d;
     if (d2h_bytes) *d2h_bytes = ctx->copied_d2h;
     return GB_OK;
+}
+
+uint32_t gb_debug_word(int reset)
+{
+    uint32_t first = 0;
+    for (auto reader : gb::debug_readers()) {
+        const uint32_t v = reader(reset != 0);
+        if (v && !first) first = v;
+    }
+    return first;
+}
+
+int gb_debug_build(void)
+{
+#ifdef GB_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 void gb_alloc_stats(uint64_t* count, uint64_t* bytes)

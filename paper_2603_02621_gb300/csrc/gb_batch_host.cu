@@ -12,6 +12,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
 {
     if (!ctx || (count && (!lo || !hi || !results))) return fail(GB_EINVAL, "NULL argument");
     if (count == 0) return GB_OK;
+    NvtxRange call_range("gb_verify_batch");
     if (count > (1u << 24)) return fail(GB_EINVAL, "count above 2^24");
     const gb_config& cfg = ctx->cfg;
     const uint32_t P1 = P ? P : cfg.p1;

@@ -28,6 +28,45 @@ constexpr uint32_t kWheelWords = kWheelW1 + kWheelW2 + kWheelW3 + kWheelW4;   //
 constexpr uint32_t kStampedPrimes = 14u;    // 3 .. 43 come from the stamp
 constexpr uint32_t kFirstStrikeIdx = 14u;   // index of 47 in 2,3,5,7,...,43,47,...
 
+// Debug builds (-DGB_DEBUG): device-side bounds checks.  GB_DCHECK(cond,
+// site) is cond; when it is false the check records the first failing site
+// (a kDbg* code) in a device word of its translation unit and the caller
+// skips the access -- no trap, the context stays usable.  gb_debug_word reads
+// (and may clear) the words of every translation unit.  Release builds:
+// always true, no code.
+enum {
+    kDbgTileStrike = 1, kDbgMidStrike = 2, kDbgLargeStrike = 3, kDbgCarryStrike = 4, kDbgCarryRing = 5,
+};
+#ifdef GB_DEBUG
+int debug_register(uint32_t (*reader)(bool reset));
+namespace {
+__device__ unsigned int g_debug_word = 0;
+uint32_t debug_read_tu(bool reset)
+{
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_debug_word, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (reset) {
+        const unsigned int z = 0;
+        cudaMemcpyToSymbol(g_debug_word, &z, sizeof z);
+    }
+    return v;
+}
+const int g_debug_registered = debug_register(debug_read_tu);
+}  // namespace
+#define GB_DCHECK(cond, site) ((cond) || (atomicCAS(&::gb::g_debug_word, 0u, (unsigned)(site)), false))
+#else
+#define GB_DCHECK(cond, site) true
+#endif
+
+// Host-side fault injection (gb_fault.cu): fault_hit counts one event of the
+// kind (GB_FAULT_ALLOC, _SUBMIT, _CANCEL) and is true for the one the spec in
+// force makes fail; fault_from_env applies GB_FAULT once per process.
+bool fault_hit(int kind);
+void fault_from_env();
+
 // Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
 // looked up once per device ordinal); grids of persistent or grid-stride
 // kernels are sized as multiples of it.  1 if the query fails.
@@ -98,6 +137,34 @@ cudaError_t launch_large(const LargeArgs& a, cudaStream_t s);
 // bit_hi unused, the whole window)
 constexpr uint32_t kMidSliceLog2 = 20;
 cudaError_t launch_mid(const LargeArgs& a, uint64_t nbits, cudaStream_t s);
+// Primes from the slice limit to sqrt(B) over a window of several chunks of
+// 2^chunk_log2 bits (gb_large.cu): each prime started once per window and
+// carried from chunk to chunk -- per-prime next-multiple words for the primes
+// below half a chunk, a ring of per-chunk buckets for the larger ones -- with
+// the multiples m p, m coprime to 30, struck by global atomic AND.
+struct BucketLargeArgs {
+    int64_t  B;                 // odd number of bit 0 of the window, with p^2 <= B for every prime
+    uint64_t nbits;             // window bits
+    uint32_t chunk_log2;        // chunk bits 2^chunk_log2 (<= 2^28)
+    uint32_t nchunks;           // ceil(nbits / chunk)
+    uint32_t B_mod30;           // B mod 30
+    const uint32_t* primes;     // [0, n_dense): below half a chunk; then n_sparse larger ones
+    const uint64_t* recip;      // their Barrett reciprocals
+    uint32_t n_dense, n_sparse;
+    uint32_t* dstate;           // [n_dense]: next multiple's offset in the current chunk | wheel position << 29
+    uint64_t* ring;             // [R][grid][cap] entries: p << 32 | wheel position << 28 | offset in the chunk
+    uint32_t* ring_cnt;         // [R][grid] entries per bucket column (zeroed before the start kernel)
+    uint32_t ring_mask;         // R - 1; R > 1 + 3 max(p) / chunk + 1, R <= kCarryMaxRing
+    uint32_t grid;              // CTAs of every launch (carry_grid()): one bucket column each
+    uint32_t cap;               // entries per bucket column
+    uint32_t* out;              // window words
+    unsigned long long* strikes;    // optional work count
+    unsigned int* spills;       // entries that found their column full (struck through to the window end)
+};
+constexpr uint32_t kCarryMaxRing = 64;
+uint32_t carry_grid();
+cudaError_t launch_large_start(const BucketLargeArgs& a, cudaStream_t s);
+cudaError_t launch_large_chunk(const BucketLargeArgs& a, uint32_t c, cudaStream_t s);
 // population count of n 32-bit words, added to *count
 cudaError_t launch_popcount(const uint32_t* words, uint64_t n, unsigned long long* count, cudaStream_t s);
 

@@ -14,10 +14,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gb.h"
 #include "gb_internal.cuh"
 
 enum { kProfSieve = 0, kProfCover = 1, kProfRetry = 2, kProfReduce = 3, kProfLarge = 4 };
+
+// an NVTX range over a scope (host timeline of a profiler such as Nsight
+// Systems: which call, slab and phase issued the launches; free when no tool
+// is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // record msg as the calling thread's last error (gb_last_error) and return code
 int fail(int code, const std::string& msg);
@@ -44,6 +56,7 @@ struct DevBuf {
     int ensure(size_t bytes)
     {
         if (bytes <= cap) return GB_OK;
+        if (gb::fault_hit(GB_FAULT_ALLOC)) return fail(GB_ENOMEM, "cudaMalloc: injected failure (GB_FAULT alloc)");
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
@@ -88,6 +101,7 @@ struct HostBuf {
     int ensure(size_t bytes)
     {
         if (bytes <= cap) return GB_OK;
+        if (gb::fault_hit(GB_FAULT_ALLOC)) return fail(GB_ENOMEM, "cudaMallocHost: injected failure (GB_FAULT alloc)");
         if (p) cudaFreeHost(p);
         p = nullptr;
         cap = 0;
@@ -143,9 +157,15 @@ struct gb_ctx {
     DevBuf part_p, part_rev, part_out;  // partition counts: prime bits, reversed bits, counts
     HostBuf hstage;
     bool batch_graph = true;          // batch kernels as one CUDA graph (GB_BATCH_GRAPH=0: plain launches)
-    // bucket sieve of the primes >= 2^20 (GB_LARGE=bucket); by default they
-    // are struck by global atomics, measured faster on GB300
+    // bucket sieve of the primes >= 2^20 (GB_LARGE=bucket): per-tile hit
+    // lists applied in shared memory; by default they are struck by global
+    // atomics, measured faster on GB300
     bool bucket_large = false;
+    // primes from mid_limit to sqrt(B) carried from chunk to chunk (gb_large.cu)
+    // for windows of at least two chunks (GB_LARGE=atomic: restarted per chunk)
+    bool carry_large = true;
+    DevBuf cstate, cring, ccnt;       // dense next-multiple words; bucket ring; bucket counts + spill count
+    uint64_t carry_spills = 0;        // entries struck through because their bucket was full (diagnostic)
     bool fused = false;               // sieve and block cover fused per CTA (GB_FUSED=1)
     uint32_t mid_limit = 1u << 20;    // primes from the split below this: per 2^20-bit slice (GB_MID_LOG2; 0 = off)
     uint32_t fill_grid = 0;           // persistent fill CTAs
@@ -214,8 +234,16 @@ struct gb_ctx {
         cudaEventCreate(&e);
         return e;
     }
+    // every phase is also an NVTX range named after its kind (a range left
+    // open by an error return is closed by the next phase)
+    bool nvtx_open = false;
     void prof_begin(int kind, uint64_t units)
     {
+        static const char* const kNvtx[GB_PROF_KINDS] = {"gb/sieve", "gb/cover", "gb/retry", "gb/reduce",
+                                                         "gb/large-primes"};
+        if (nvtx_open) nvtxRangePop();
+        nvtxRangePushA(kNvtx[kind]);
+        nvtx_open = true;
         if (!profiling) return;
         cur_kind = kind;
         cur_a = take_event();
@@ -226,6 +254,8 @@ struct gb_ctx {
     }
     void prof_end()
     {
+        if (nvtx_open) nvtxRangePop();
+        nvtx_open = false;
         if (!profiling || cur_kind < 0) return;
         cudaEvent_t b = take_event();
         cudaEventRecordWithFlags(b, capturing ? cap_stream : stream,

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include "gb.h"
+#include "gb_internal.cuh"
 
 struct gb_server {
     struct Pending {
@@ -104,6 +105,30 @@ void post(gb_server* s, const std::vector<gb_server::Pending>& batch, int rc, do
     }
     s->cv_done.notify_all();
     s->cv_work.notify_all();
+}
+
+// with s->mu held: take the ticket's request out of its queue and post a
+// GB_ECANCELED response; GB_EBUSY if it is no longer queued
+int cancel_locked(gb_server* s, uint64_t ticket)
+{
+    for (std::deque<gb_server::Pending>* q : {&s->queue, &s->qqueue}) {
+        for (auto it = q->begin(); it != q->end(); ++it) {
+            if (it->ticket != ticket) continue;
+            gb_response r{};
+            r.status = GB_ECANCELED;
+            r.t_submit_us = it->t_submit;
+            r.t_start_us = r.t_done_us = s->now_us();
+            if (it->req.kind == GB_REQ_RANGE) {
+                r.range.lo = it->req.lo;
+                r.range.hi = it->req.hi;
+            }
+            s->done[ticket] = r;
+            s->n_done += 1;
+            q->erase(it);
+            return GB_OK;
+        }
+    }
+    return GB_EBUSY;
 }
 
 // a range lane: admits ranges from the head of the queue within the budget
@@ -245,6 +270,8 @@ extern "C" int gb_server_submit(gb_server* s, const gb_request* req, uint64_t* t
     if (!s || !req || !ticket) return GB_EINVAL;
     const int rc = check_request(s, *req);
     if (rc) return rc;
+    if (gb::fault_hit(GB_FAULT_SUBMIT)) return GB_EBUSY;            // refused at admission (injected)
+    const bool cancel_now = gb::fault_hit(GB_FAULT_CANCEL);         // cancelled once queued (injected)
     gb_config cfg{};
     gb_get_config(s->lanes[0], &cfg);
     {
@@ -254,10 +281,28 @@ extern "C" int gb_server_submit(gb_server* s, const gb_request* req, uint64_t* t
         const gb_server::Pending p{*ticket, *req, request_bytes(*req, std::max(cfg.p1, cfg.p2)), s->now_us()};
         (req->kind == GB_REQ_QUERY ? s->qqueue : s->queue).push_back(p);
         s->n_submitted += 1;
+        if (cancel_now) cancel_locked(s, *ticket);
     }
+    if (cancel_now) s->cv_done.notify_all();
     if (req->kind == GB_REQ_QUERY) s->cv_query.notify_one();
     else s->cv_work.notify_one();
     return GB_OK;
+}
+
+extern "C" int gb_server_cancel(gb_server* s, uint64_t ticket)
+{
+    if (!s) return GB_EINVAL;
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (ticket == 0 || ticket >= s->next_ticket) return GB_EINVAL;
+        rc = cancel_locked(s, ticket);
+    }
+    if (rc == GB_OK) {
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
+    return rc;
 }
 
 extern "C" int gb_server_wait(gb_server* s, uint64_t ticket, gb_response* out, uint32_t timeout_ms)

@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(256) k_large(const LargeArgs a)
         }
         for (; i < span; i += p) {
             const uint64_t bit = a.bit_lo + i;
-            atomicAnd(a.out + (bit >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, (uint32_t)bit));
+            if (GB_DCHECK(bit < a.bit_hi, kDbgLargeStrike))
+                atomicAnd(a.out + (bit >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, (uint32_t)bit));
             ++nstrike;
         }
     }
@@ -262,18 +263,40 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
     __syncthreads();
     const int64_t b = B + 2 * (int64_t)t0;
     const int64_t last = B + 2 * (int64_t)(t0 + nb - 1);
-    for (uint32_t k = threadIdx.x; k < n_primes; k += blockDim.x) {
-        const uint32_t p = primes[k];
-        const uint64_t pp = (uint64_t)p * p;
-        if ((int64_t)pp > last) break;                       // ascending primes
-        uint32_t i = first_odd_multiple(b, p, recip[k]);
-        if ((int64_t)pp > b) {
-            const uint64_t isq = ((uint64_t)((int64_t)pp - b)) >> 1;
-            if (isq > i) i = (uint32_t)isq;                   // isq < nb here
+    // four primes per thread at a time (k, k + T, k + 2T, k + 3T): their loads
+    // and Barrett starts are independent, so their latencies overlap
+    constexpr int U = 4;
+    const uint32_t T = blockDim.x;
+    for (uint32_t k0 = threadIdx.x; k0 < n_primes; k0 += U * T) {
+        uint32_t p[U], i[U];
+        uint64_t m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t k = k0 + u * T;
+            p[u] = k < n_primes ? primes[k] : 0u;
+            m[u] = k < n_primes ? recip[k] : 0ull;
         }
-        for (; i < nb; i += p) {                              // p < 2^31, i < 2^20: no wrap
-            atomicAnd(slice + (i >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, i));
-            ++nstrike;
+        if ((int64_t)((uint64_t)p[0] * p[0]) > last) break;  // ascending primes
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            i[u] = nb;                                        // no strike
+            const uint64_t pp = (uint64_t)p[u] * p[u];
+            if (p[u] && (int64_t)pp <= last) {
+                uint32_t s = first_odd_multiple(b, p[u], m[u]);
+                if ((int64_t)pp > b) {
+                    const uint64_t isq = ((uint64_t)((int64_t)pp - b)) >> 1;
+                    if (isq > s) s = (uint32_t)isq;           // isq < nb here
+                }
+                i[u] = s;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            for (uint32_t j = i[u]; j < nb; j += p[u]) {      // p < 2^31, j < 2^20: no wrap
+                if (GB_DCHECK(j < (1u << kMidSliceLog2), kDbgMidStrike))
+                    atomicAnd(slice + (j >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, j));
+                ++nstrike;
+            }
         }
     }
     __syncthreads();

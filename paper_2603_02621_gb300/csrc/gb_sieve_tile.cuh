@@ -14,10 +14,19 @@ __device__ __forceinline__ uint32_t pmod_u32(int64_t x, uint32_t M)
 
 // clear bit i of the tile: word i/32 at byte offset (i >> 3) & ~3, mask
 // ~(1 << (i & 31)) as a rotate of 0xfffffffe (the funnel shift takes i mod 32)
-__device__ __forceinline__ void strike(uint32_t* sm, uint32_t i)
+// (tile_bits: the tile's size, for the bounds check of a debug build)
+__device__ __forceinline__ void strike(uint32_t* sm, uint32_t i, uint32_t tile_bits)
 {
+    if (!GB_DCHECK(i < tile_bits, kDbgTileStrike)) return;
     atomicAnd(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sm) + ((i >> 3) & ~3u)),
               __funnelshift_l(0xfffffffeu, 0xfffffffeu, i));
+}
+
+// clear the bits of mask in tile word w (tile_words: the tile's size in words)
+__device__ __forceinline__ void strike_word(const uint32_t* sm, uint32_t* w, uint32_t mask, uint32_t tile_words)
+{
+    if (!GB_DCHECK((uint32_t)(w - sm) < tile_words, kDbgTileStrike)) return;
+    atomicAnd(w, mask);
 }
 
 // one stamp table read at pattern offset a (a < period): 32 bits from bit a
@@ -83,6 +92,8 @@ __device__ __forceinline__ void sieve_tile(const SieveArgs& a, uint64_t t0, cons
 
     // 2. strikes of the primes 47 <= p with p^2 <= the tile's last number
     const int64_t last = b + 2 * (int64_t)(nb - 1);
+    const uint32_t tw = a.tile_bits / 32;             // tile words (bounds of a debug build)
+    (void)tw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long nstrike = 0;
     // 2a. small primes, one warp each: warp w takes the primes w, w + NW, ...;
@@ -116,34 +127,54 @@ __device__ __forceinline__ void sieve_tile(const SieveArgs& a, uint64_t t0, cons
                 uint32_t* w = sm + (i >> 5);
                 uint32_t* const end = sm + ((nb - (i & 31u) + 31u) >> 5);   // words whose bit i&31 is < nb
                 for (; w + 3 * q < end; w += 4 * q) {
-                    atomicAnd(w, mask);
-                    atomicAnd(w + q, mask);
-                    atomicAnd(w + 2 * q, mask);
-                    atomicAnd(w + 3 * q, mask);
+                    strike_word(sm, w, mask, tw);
+                    strike_word(sm, w + q, mask, tw);
+                    strike_word(sm, w + 2 * q, mask, tw);
+                    strike_word(sm, w + 3 * q, mask, tw);
                 }
-                for (; w < end; w += q) atomicAnd(w, mask);
+                for (; w < end; w += q) strike_word(sm, w, mask, tw);
             }
         }
     }
-    // 2b. larger primes, one thread each
-    for (uint32_t k = a.n_warp + threadIdx.x; k < a.n_primes; k += NT) {
-        const uint32_t p = a.primes[k];
-        const uint64_t pp = (uint64_t)p * p;
-        if ((int64_t)pp > last) break;
-        uint32_t i = first_odd_multiple(b, p, a.recip[k]);
-        if ((int64_t)pp > b) {
-            uint32_t isq = (uint32_t)(((int64_t)pp - b) >> 1);
-            if (isq > i) i = isq;
+    // 2b. larger primes, one thread each; four at a time per thread (k, k +
+    // NT, k + 2 NT, k + 3 NT), so that their loads and Barrett starts overlap
+    constexpr int U = 4;
+    for (uint32_t k0 = a.n_warp + threadIdx.x; k0 < a.n_primes; k0 += U * NT) {
+        uint32_t p[U], s[U];
+        uint64_t m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t k = k0 + u * NT;
+            p[u] = k < a.n_primes ? a.primes[k] : 0u;
+            m[u] = k < a.n_primes ? a.recip[k] : 0ull;
         }
-        if (a.strikes && i < nb) nstrike += (nb - 1 - i) / p + 1;
-        // i < 2^20 and p < 3.1e9 (p^2 < 2^63): i + p cannot wrap
-        if (p < (1u << 20)) {
-            for (; i + p < nb; i += 2 * p) {
-                strike(sm, i);
-                strike(sm, i + p);
+        if ((int64_t)((uint64_t)p[0] * p[0]) > last) break;    // ascending primes
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            s[u] = nb;                                          // no strike
+            const uint64_t pp = (uint64_t)p[u] * p[u];
+            if (p[u] && (int64_t)pp <= last) {
+                uint32_t i = first_odd_multiple(b, p[u], m[u]);
+                if ((int64_t)pp > b) {
+                    const uint32_t isq = (uint32_t)(((int64_t)pp - b) >> 1);
+                    if (isq > i) i = isq;
+                }
+                s[u] = i;
+                if (a.strikes && i < nb) nstrike += (nb - 1 - i) / p[u] + 1;
             }
         }
-        for (; i < nb; i += p) strike(sm, i);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            uint32_t i = s[u];
+            // i < 2^20 and p < 3.1e9 (p^2 < 2^63): i + p cannot wrap
+            if (p[u] < (1u << 20)) {
+                for (; i + p[u] < nb; i += 2 * p[u]) {
+                    strike(sm, i, a.tile_bits);
+                    strike(sm, i + p[u], a.tile_bits);
+                }
+            }
+            for (; i < nb; i += p[u]) strike(sm, i, a.tile_bits);
+        }
     }
     if (a.strikes) {
         for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);

@@ -10,8 +10,11 @@
 // not depend on any of these settings, so the search never changes a result.
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -79,7 +82,76 @@ double time_setting(gb_ctx* ctx, const gb_config& cfg, const uint64_t* lo, const
     return best;
 }
 
+// key of a tuning result: the GPU (name and SM count), the mode, the
+// settings that are not tuned (base primes, P2, slab) and the sample itself
+// (count and an FNV-1a hash of its bounds)
+std::string tune_key(const gb_config& c, int mode, const uint64_t* lo, const uint64_t* hi, uint32_t count)
+{
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, c.device) != cudaSuccess) {
+        cudaGetLastError();
+        std::snprintf(prop.name, sizeof prop.name, "unknown");
+    }
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](uint64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (v >> (8 * b)) & 0xff;
+            h *= 1099511628211ull;
+        }
+    };
+    for (uint32_t i = 0; i < count; ++i) {
+        mix(lo[i]);
+        mix(hi[i]);
+    }
+    std::string name(prop.name);
+    for (char& ch : name)
+        if (ch == '|' || ch == '\t' || ch == '\n') ch = '_';
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "%s|%d|%d|%u|%016llx|%llu|%u|%llu", name.c_str(), prop.multiProcessorCount, mode,
+                  count, (unsigned long long)h, (unsigned long long)c.base_limit, c.p2,
+                  (unsigned long long)c.slab_bits);
+    return buf;
+}
+
 }  // namespace
+
+extern "C" int gb_tune_cache_lookup(const char* path, const char* key, gb_config* cfg, double* best_ms)
+{
+    if (!path || !key || !cfg) return GB_EINVAL;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return GB_ERANGE;
+    char line[1024];
+    int found = GB_ERANGE;
+    const size_t klen = std::strlen(key);
+    while (std::fgets(line, sizeof line, f)) {
+        if (std::strncmp(line, key, klen) != 0 || line[klen] != '\t') continue;
+        unsigned tile = 0, split = 0, p1 = 0, prefix = 0, seg = 0, cta = 0;
+        double ms = 0;
+        if (std::sscanf(line + klen + 1, "%u %u %u %u %u %u %lf", &tile, &split, &p1, &prefix, &seg, &cta, &ms) != 7)
+            continue;                                      // a damaged line is skipped
+        cfg->tile_bits = tile;
+        cfg->bucket_split = split;
+        cfg->p1 = p1;
+        cfg->cover_prefix = prefix;
+        cfg->seg_len = seg;
+        cfg->cta_threads = cta;
+        if (best_ms) *best_ms = ms;
+        found = GB_OK;                                     // the last entry for a key wins
+    }
+    std::fclose(f);
+    return found;
+}
+
+extern "C" int gb_tune_cache_store(const char* path, const char* key, const gb_config* cfg, double best_ms)
+{
+    if (!path || !key || !cfg || std::strchr(key, '\t') || std::strchr(key, '\n')) return GB_EINVAL;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return GB_EINVAL;
+    const int n = std::fprintf(f, "%s\t%u %u %u %u %u %u %.6f\n", key, cfg->tile_bits, cfg->bucket_split, cfg->p1,
+                               cfg->cover_prefix, cfg->seg_len, cfg->cta_threads, best_ms);
+    const int rc = std::fclose(f);
+    return (n > 0 && rc == 0) ? GB_OK : GB_EINVAL;
+}
 
 extern "C" int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_t count, int mode,
                            uint32_t reps, gb_config* out, double* best_ms)
@@ -91,6 +163,19 @@ extern "C" int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, 
     int rc = gb_get_config(ctx, &best);
     if (rc) return rc;
     const gb_config start = best;
+    // a result for this GPU, mode, setting and sample in the cache file
+    const char* cache = std::getenv("GB_TUNE_CACHE");
+    std::string key;
+    if (cache && *cache) {
+        key = tune_key(best, mode, lo, hi, count);
+        gb_config hitc = best;
+        double ms = 0;
+        if (gb_tune_cache_lookup(cache, key.c_str(), &hitc, &ms) == GB_OK && gb_set_config(ctx, &hitc) == GB_OK) {
+            if (out) *out = hitc;
+            if (best_ms) *best_ms = ms;
+            return GB_OK;
+        }
+    }
     std::vector<gb_segment_result> recs(mode == GB_TUNE_BATCH ? count : 0);
     Timer t;
     int err = GB_OK;
@@ -165,6 +250,7 @@ extern "C" int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, 
     }
     rc = gb_set_config(ctx, &best);
     if (rc) return rc;
+    if (!key.empty()) gb_tune_cache_store(cache, key.c_str(), &best, best_t);   // a cache that cannot be written is skipped
     if (out) *out = best;
     if (best_ms) *best_ms = best_t;
     return GB_OK;

@@ -11,6 +11,7 @@ extern "C" {
 int gb_verify_range(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P, gb_range_result* out)
 {
     if (!ctx || !out) return fail(GB_EINVAL, "NULL argument");
+    NvtxRange call_range("gb_verify_range");
     if ((lo & 1) || (hi & 1) || lo < 4 || hi <= lo) return fail(GB_EINVAL, "range must be even, lo >= 4, hi > lo");
     if (hi > GB_MAX_HI) return fail(GB_EINVAL, "hi beyond 2^63 - 2^26");
     const gb_config& cfg = ctx->cfg;

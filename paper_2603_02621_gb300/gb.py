@@ -18,7 +18,8 @@ import numpy as np
 
 from .build import LIB
 
-GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ETIMEOUT, GB_EBUSY, GB_ERANGE = range(7)
+GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_ETIMEOUT, GB_EBUSY, GB_ERANGE, GB_ECANCELED = range(8)
+GB_FAULT_ALLOC, GB_FAULT_SUBMIT, GB_FAULT_CANCEL = 0, 1, 2
 GB_MAX_HI = (1 << 63) - (1 << 26)      # largest hi of a range (include/gb.h)
 
 
@@ -86,6 +87,13 @@ SIGNATURES = {
     "gb_server_stats": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), POINTER(c_uint64),
                                 POINTER(c_uint64)]),
     "gb_server_destroy": (None, [c_void_p]),
+    "gb_server_cancel": (c_int, [c_void_p, c_uint64]),
+    "gb_fault_set": (c_int, [c_char_p]),
+    "gb_fault_tick": (c_int, [c_int]),
+    "gb_debug_word": (c_uint32, [c_int]),
+    "gb_debug_build": (c_int, []),
+    "gb_tune_cache_lookup": (c_int, [c_char_p, c_char_p, POINTER(gb_config), POINTER(ctypes.c_double)]),
+    "gb_tune_cache_store": (c_int, [c_char_p, c_char_p, POINTER(gb_config), ctypes.c_double]),
     "gb_autotune": (c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), c_uint32, c_int, c_uint32,
                             POINTER(gb_config), POINTER(ctypes.c_double)]),
     "gb_profile_enable": (c_int, [c_void_p, c_int]),
@@ -104,12 +112,14 @@ _lib = None
 
 
 def load(path: str | None = None) -> ctypes.CDLL:
-    """Load libgb.so (no fallback: a missing library is an error)."""
+    """Load libgb.so (no fallback: a missing library is an error).  The
+    environment variable GB_LIBRARY names another build of the same library
+    (the debug build, libgb_debug.so) to load instead."""
     global _lib
     with _lock:
         if _lib is not None and path is None:
             return _lib
-        p = path or LIB
+        p = path or os.environ.get("GB_LIBRARY") or LIB
         if not os.path.exists(p):
             raise ImportError(f"libgb.so not built at {p}: run python -m paper_2603_02621_gb300.build")
         lib = ctypes.CDLL(p)
@@ -349,6 +359,36 @@ def gb_profile_copies(ctx: int) -> dict:
     return dict(h2d=a.value, d2h=b.value)
 
 
+def gb_fault_set(spec: str | None) -> None:
+    """Host-side fault injection (gb.h): "kind@n[,kind@n...]", kind alloc,
+    submit or cancel; None or "" clears."""
+    _check(load().gb_fault_set(spec.encode() if spec else None), "gb_fault_set")
+
+
+def gb_fault_tick(kind: int) -> bool:
+    return bool(load().gb_fault_tick(kind))
+
+
+def gb_tune_cache_lookup(path: str, key: str):
+    """(config fields dict, best ms) stored for key in the autotune cache
+    file, or None."""
+    c = gb_config()
+    ms = ctypes.c_double()
+    rc = load().gb_tune_cache_lookup(path.encode(), key.encode(), ctypes.byref(c), ctypes.byref(ms))
+    if rc == GB_ERANGE:
+        return None
+    _check(rc, "gb_tune_cache_lookup")
+    return {f: getattr(c, f) for f in ("tile_bits", "bucket_split", "p1", "cover_prefix", "seg_len",
+                                       "cta_threads")}, ms.value
+
+
+def gb_tune_cache_store(path: str, key: str, fields: dict, best_ms: float) -> None:
+    c = gb_config()
+    for k, v in fields.items():
+        setattr(c, k, v)
+    _check(load().gb_tune_cache_store(path.encode(), key.encode(), ctypes.byref(c), best_ms), "gb_tune_cache_store")
+
+
 def gb_alloc_stats() -> dict:
     """Device and pinned host allocations the library has made in this process."""
     a, b = c_uint64(), c_uint64()
@@ -483,6 +523,10 @@ class Server:
         t = c_uint64()
         _check(load().gb_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "gb_server_submit")
         return t.value
+
+    def cancel(self, ticket: int) -> int:
+        """Cancel a request still in its queue (GB_OK), else GB_EBUSY."""
+        return _check(load().gb_server_cancel(self.handle, ticket), "gb_server_cancel", allow=(GB_EBUSY,))
 
     def wait(self, ticket: int, timeout_ms: int = 600000) -> dict:
         r = gb_response()

@@ -183,3 +183,24 @@ def test_batch_graph_and_plain_launches_agree(gbm, monkeypatch):
             outs.append(a)
     assert outs[0]["records"] == outs[1]["records"]
     np.testing.assert_array_equal(outs[0]["hist"], outs[1]["hist"])
+
+
+def test_autotune_cache_hit(gbm, monkeypatch, tmp_path):
+    """With GB_TUNE_CACHE set, a second autotune of the same sample on the
+    same GPU applies the stored setting without timing anything."""
+    import time
+    from paper_2603_02621_gb300.workloads import batched_ranges
+    ranges = batched_ranges(count=32, seed=4, log2_min=10, log2_max=16, start_min=10**9, start_max=10**12)
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("GB_TUNE_CACHE", str(path))
+    with gbm.Context(device=0, base_limit=1 << 20, seg_len=1 << 20, p1=P1, p2=P2) as g:
+        before = g.verify_batch(ranges, hist_stride=512)
+        cfg1, ms1 = g.autotune(ranges, gbm.GB_TUNE_BATCH, reps=1)
+        t0 = time.perf_counter()
+        cfg2, ms2 = g.autotune(ranges, gbm.GB_TUNE_BATCH, reps=1)
+        assert time.perf_counter() - t0 < 0.5
+        assert cfg2 == cfg1 and ms2 == pytest.approx(ms1, rel=1e-6)
+        after = g.verify_batch(ranges, hist_stride=512)
+        assert after["records"] == before["records"]
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith(torch.cuda.get_device_name(0) + "|")

@@ -82,3 +82,50 @@ def test_strike_counters_equal_the_oracle(gbm, monkeypatch, oracle, A, nbits, mo
         gbm.gb_profile_enable(g.handle, False)
     last = A + 2 * (nbits - 1)
     assert w["sieve_strikes"] + w["large_strikes"] == oracle.count_strikes(A, nbits, 47, math.isqrt(last))
+
+
+@pytest.mark.parametrize("A,nbits", [
+    (4 * 10**18 - 10**11 + 1, (1 << 30) + 12345),    # dense and bucketed primes, four chunks and a ragged tail
+    (10**15 + 1, (1 << 29) + 777),                    # every carried prime below half a chunk
+    (10**14 + 1, (1 << 31) + 64),                     # the top primes have p^2 inside the window
+    ((1 << 62) - (1 << 30) + 1, (1 << 29) + 5),       # primes up to 2^31: the widest bucket ring
+])
+def test_carry_equals_atomic(gbm, monkeypatch, oracle, A, nbits):
+    """The large primes started once per window and carried from chunk to
+    chunk (default; multiples m p with m coprime to 30) give the same bits as
+    the per-chunk restart with every odd multiple (GB_LARGE=atomic), and
+    sampled bits agree with the oracle's Miller-Rabin."""
+    monkeypatch.delenv("GB_LARGE", raising=False)
+    with gbm.Context(device=0, base_limit=1 << 31, p1=1 << 15, p2=1 << 20) as g:
+        qc, pc = _sieve(g, A, nbits)
+    with _ctx(gbm, monkeypatch, "atomic") as g:
+        qa, pa = _sieve(g, A, nbits)
+    np.testing.assert_array_equal(qc, qa)
+    assert pc == pa
+    from paper_2603_02621_gb300.workloads import sample_indices
+    bits = np.unpackbits(qc.view(np.uint8), bitorder="little")
+    for i in sample_indices(nbits, 2000, seed=7):
+        assert bool(bits[i]) == oracle.mr_isprime(A + 2 * i), i
+
+
+@pytest.mark.parametrize("A,nbits", [
+    (4 * 10**18 - 10**11 + 1, (1 << 29) + 64),
+    (10**14 + 1, (1 << 30) + 64),
+])
+def test_carry_strike_counter_equals_the_oracle(gbm, monkeypatch, oracle, A, nbits):
+    """The work counted by the carried large primes: strikes of m p with m
+    coprime to 15 for the primes from 2^20 to sqrt(A); below 2^20 (tile and
+    slices) and above sqrt(A) (p^2 inside the window) every odd multiple."""
+    import math
+    monkeypatch.delenv("GB_LARGE", raising=False)
+    with gbm.Context(device=0, base_limit=1 << 31, p1=1 << 15, p2=1 << 20) as g:
+        q = torch.zeros(((nbits + 63) // 64,), dtype=torch.int64, device="cuda")
+        gbm.gb_profile_enable(g.handle, True)
+        g.sieve_segment(A, nbits, q)
+        w = gbm.gb_profile_work(g.handle)
+        gbm.gb_profile_enable(g.handle, False)
+    last = A + 2 * (nbits - 1)
+    r0, r1 = math.isqrt(A), math.isqrt(last)
+    want = (oracle.count_strikes(A, nbits, 47, (1 << 20) - 1) + oracle.count_strikes_coprime15(A, nbits, 1 << 20, r0)
+            + oracle.count_strikes(A, nbits, r0 + 1, r1))
+    assert w["sieve_strikes"] + w["large_strikes"] == want
