@@ -6,7 +6,7 @@
 //                -> compaction to the ascending prime list with Barrett
 //                reciprocals; L = max(base_limit, p1, p2)
 //   run_sieve    a q window: tile sieve of the primes below the split, then
-//                the primes above it by 2^20-bit slices in shared memory (to
+//                the primes above it by 224 KB slices in shared memory (to
 //                the mid limit) and by L2-resident chunks or bucket lists
 //
 // The verification entry points are in gb_verify.cu (gb_verify_range),
@@ -154,7 +154,7 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
         la.n_primes = (uint32_t)(np - nsmall);
         la.out = out;
         la.strikes = ctx->work_ptr(2);
-        // primes below mid_limit: per 2^20-bit slice in shared memory
+        // primes below mid_limit: per shared-memory slice of the window
         uint64_t nmid = nsmall;
         const int64_t last = B + 2 * (int64_t)(nbits - 1);
         if (ctx->mid_limit > ctx->split(isqrt_u64((uint64_t)last))) {

@@ -43,7 +43,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     if (n_sieve > 0xffffffffull || n_cover > 0xffffffffull) return fail(GB_EINVAL, "batch too large");
 
     // large primes: np primes <= sqrt of the batch's last number; those below
-    // the split strike per tile, those below the mid limit per 2^20-bit slice
+    // the split strike per tile, those below the mid limit per 224 KB slice
     // of each window in shared memory, the rest per window piece by atomics
     const uint64_t np = ctx->pi(isqrt_u64(last_max));
     const uint32_t split = ctx->split(isqrt_u64(last_max));
@@ -55,7 +55,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
     if (nmid > nsmall)
         for (uint32_t i = 0; i < count; ++i) {
             const uint64_t qw = (hi[i] - lo[i]) / 2 / 64 + 1 + H / 128 + 2;
-            n_mid += (64 * qw + (1ull << gb::kMidSliceLog2) - 1) >> gb::kMidSliceLog2;
+            n_mid += (64 * qw + gb::kMidSliceBits - 1) / gb::kMidSliceBits;
         }
     if (n_mid > 0xffffffffull) return fail(GB_EINVAL, "batch too large");
     // window pieces of at most one L2-sized chunk, grouped up to a chunk;
@@ -144,7 +144,7 @@ int gb_verify_batch(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, uint32_
             const uint64_t chunks = (((n + 31) / 32) + 2ull * cw - 1) / (2ull * cw);
             for (uint64_t c = 0; c < chunks; ++c) { c_range[ci] = i; c_chunk[ci] = (uint32_t)c; ++ci; }
             if (n_mid) {
-                const uint64_t slices = (64 * qw + (1ull << gb::kMidSliceLog2) - 1) >> gb::kMidSliceLog2;
+                const uint64_t slices = (64 * qw + gb::kMidSliceBits - 1) / gb::kMidSliceBits;
                 for (uint64_t t = 0; t < slices; ++t) { m_range[mi] = i; m_slice[mi] = (uint32_t)t; ++mi; }
             }
         }

@@ -131,11 +131,13 @@ struct LargeArgs {
     unsigned long long* strikes;    // optional work count
 };
 cudaError_t launch_large(const LargeArgs& a, cudaStream_t s);
-// the same primes struck per 2^20-bit slice of the window in shared memory
-// (one Barrett start per prime and slice): for primes up to a few slices,
-// whose strikes are dense enough to pay for the starts (LargeArgs: bit_lo /
-// bit_hi unused, the whole window)
-constexpr uint32_t kMidSliceLog2 = 20;
+// the same primes struck per slice of the window in shared memory (one
+// Barrett start per prime and slice): for primes up to a few slices, whose
+// strikes are dense enough to pay for the starts (LargeArgs: bit_lo / bit_hi
+// unused, the whole window).  A slice is 224 KB of shared memory, nearly all
+// an SM has, so that the starts -- most of the kernel's instructions -- are
+// as few as they can be.
+constexpr uint32_t kMidSliceBits = 7u << 18;
 cudaError_t launch_mid(const LargeArgs& a, uint64_t nbits, cudaStream_t s);
 // Primes from the slice limit to sqrt(B) over a window of several chunks of
 // 2^chunk_log2 bits (gb_large.cu): each prime started once per window and
@@ -344,7 +346,7 @@ struct CoverItemsArgs {
 };
 cudaError_t launch_cover_items(const CoverItemsArgs& a, int KA, cudaStream_t s);
 
-// primes from the split below the mid limit over (range, 2^20-bit slice)
+// primes from the split below the mid limit over (range, shared-memory slice)
 // items of a batch, in shared memory
 struct MidItemsArgs {
     const BatchRange* ranges;

@@ -129,7 +129,12 @@ __device__ __forceinline__ void add_strikes(const BucketLargeArgs& a, unsigned l
 __global__ void __launch_bounds__(kThreads) k_large_start(const BucketLargeArgs a)
 {
     __shared__ uint32_t s_cnt[kCarryMaxRing];
-    load_counts(a, s_cnt, 0xffffffffu);
+    __shared__ uint8_t s_inv[30], s_next[30];             // the tables, where lanes may read different entries
+    if (threadIdx.x < 30) {
+        s_inv[threadIdx.x] = kInv30[threadIdx.x];
+        s_next[threadIdx.x] = kNext30[threadIdx.x];
+    }
+    load_counts(a, s_cnt, 0xffffffffu);                   // (ends with a barrier)
     const uint32_t n = a.n_dense + a.n_sparse;
     const uint32_t stride = gridDim.x * blockDim.x;
     unsigned long long nstrike = 0;
@@ -142,8 +147,8 @@ __global__ void __launch_bounds__(kThreads) k_large_start(const BucketLargeArgs 
             const uint64_t i0 = first_odd_multiple(a.B, p, a.recip[k]);        // < p
             // m0 = (B + 2 i0) / p is odd; its residue mod 30 from (B + 2 i0) mod 30
             const uint32_t r = (a.B_mod30 + 2u * (uint32_t)(i0 % 15u)) % 30u;
-            const uint32_t mr = (r * (uint32_t)kInv30[p % 30u]) % 30u;
-            const uint32_t nx = kNext30[mr];
+            const uint32_t mr = (r * (uint32_t)s_inv[p % 30u]) % 30u;
+            const uint32_t nx = s_next[mr];
             w = nx & 0xfu;
             const uint64_t i = i0 + (uint64_t)p * (nx >> 4);                 // < 3p
             if (k < a.n_dense) {

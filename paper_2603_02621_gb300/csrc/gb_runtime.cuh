@@ -167,7 +167,7 @@ struct gb_ctx {
     DevBuf cstate, cring, ccnt;       // dense next-multiple words; bucket ring; bucket counts + spill count
     uint64_t carry_spills = 0;        // entries struck through because their bucket was full (diagnostic)
     bool fused = false;               // sieve and block cover fused per CTA (GB_FUSED=1)
-    uint32_t mid_limit = 1u << 20;    // primes from the split below this: per 2^20-bit slice (GB_MID_LOG2; 0 = off)
+    uint32_t mid_limit = 1u << 20;    // primes from the split below this: per shared-memory slice (GB_MID_LOG2; 0 = off)
     uint32_t fill_grid = 0;           // persistent fill CTAs
     uint32_t bcap = 0;                // entries per (CTA, bucket tile) list
     uint64_t bucket_overflows = 0;    // chunks redone by the atomic kernel

@@ -245,7 +245,7 @@ cudaError_t launch_large(const LargeArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Primes between the tile split and a few 2^20-bit slices: each CTA loads one
+// Primes between the tile split and a few slices (kMidSliceBits): each CTA loads one
 // slice of the window (already sieved by the smaller primes) into shared
 // memory, strikes every such prime in it (one Barrett start per prime and
 // slice), and stores it back -- shared-memory atomics instead of one L2
@@ -255,7 +255,7 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
                                           uint32_t* slice, unsigned long long& nstrike)
 {
     const uint64_t rem = nbits - t0;
-    const uint32_t nb = rem < (1ull << kMidSliceLog2) ? (uint32_t)rem : (1u << kMidSliceLog2);
+    const uint32_t nb = rem < kMidSliceBits ? (uint32_t)rem : kMidSliceBits;
     const uint32_t nw = (nb + 31) / 32;
     uint32_t* q = words + t0 / 32;
     __syncthreads();                                          // slice free
@@ -292,8 +292,8 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            for (uint32_t j = i[u]; j < nb; j += p[u]) {      // p < 2^31, j < 2^20: no wrap
-                if (GB_DCHECK(j < (1u << kMidSliceLog2), kDbgMidStrike))
+            for (uint32_t j = i[u]; j < nb; j += p[u]) {      // p < 2^31, j < 2^21: no wrap
+                if (GB_DCHECK(j < kMidSliceBits, kDbgMidStrike))
                     atomicAnd(slice + (j >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, j));
                 ++nstrike;
             }
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(1024) k_mid(const LargeArgs a, uint64_t nbits)
 {
     extern __shared__ uint32_t slice[];
     unsigned long long nstrike = 0;
-    mid_slice(a.B, nbits, a.out, (uint64_t)blockIdx.x << kMidSliceLog2, a.primes, a.recip, a.n_primes, slice,
+    mid_slice(a.B, nbits, a.out, (uint64_t)blockIdx.x * kMidSliceBits, a.primes, a.recip, a.n_primes, slice,
               nstrike);
     if (a.strikes) {
         for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(1024) k_mid_items(const MidItemsArgs a)
         __syncthreads();
         if (item >= n_items) break;
         const BatchRange r = a.ranges[a.item_range[item]];
-        mid_slice(r.B, r.nbits, a.Q + 2 * r.q_off, (uint64_t)a.item_slice[item] << kMidSliceLog2, a.primes, a.recip,
+        mid_slice(r.B, r.nbits, a.Q + 2 * r.q_off, (uint64_t)a.item_slice[item] * kMidSliceBits, a.primes, a.recip,
                   a.n_primes, slice, nstrike);
     }
     if (a.strikes) {
@@ -343,7 +343,7 @@ cudaError_t launch_mid_items(const MidItemsArgs& a, cudaStream_t s)
     if (a.n_primes == 0) return cudaSuccess;
     if (!a.primes || !a.recip || !a.Q || !a.ranges || !a.item_range || !a.item_slice || !a.n_items || !a.head)
         return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(1u << kMidSliceLog2) / 8;
+    const size_t smem = (size_t)kMidSliceBits / 8;
     cudaError_t e = cudaFuncSetAttribute(k_mid_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -357,9 +357,9 @@ cudaError_t launch_mid(const LargeArgs& a, uint64_t nbits, cudaStream_t s)
 {
     if (a.n_primes == 0 || nbits == 0) return cudaSuccess;
     if (!a.primes || !a.recip || !a.out) return cudaErrorInvalidValue;
-    const uint64_t slices = (nbits + (1ull << kMidSliceLog2) - 1) >> kMidSliceLog2;
+    const uint64_t slices = (nbits + kMidSliceBits - 1) / kMidSliceBits;
     if (slices > 0x7fffffffull) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(1u << kMidSliceLog2) / 8;
+    const size_t smem = (size_t)kMidSliceBits / 8;
     cudaError_t e = cudaFuncSetAttribute(k_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_mid<<<(unsigned)slices, 1024, smem, s>>>(a, nbits);
