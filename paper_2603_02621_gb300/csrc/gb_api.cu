@@ -109,6 +109,7 @@ static int carry_large(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, ui
         const double M = (double)C * (8.0 / 15.0) * (std::log(std::log(p_hi)) - std::log(std::log(p_lo)) + 1.0 / p_lo) /
                          a.grid;
         a.cap = (uint32_t)std::min(2.0e9, 1.15 * M + 8.0 * std::sqrt(M) + 64.0);
+        if (ctx->carry_cap) a.cap = ctx->carry_cap;           // (test switch: small columns spill)
     }
     const size_t ncnt = (size_t)R * a.grid;
     int rc;
@@ -429,6 +430,7 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
         const int v = atoi(e);
         ctx->mid_limit = (v >= 16 && v <= 31) ? (1u << v) : 0u;
     }
+    if (const char* e = getenv("GB_CARRY_CAP")) ctx->carry_cap = (uint32_t)std::strtoul(e, nullptr, 10);
     if (const char* e = getenv("GB_LARGE_CHUNK_LOG2")) {
         const int v = atoi(e);
         if (v >= 16 && v <= 40) ctx->large_chunk_bits = 1ull << v;
@@ -465,6 +467,7 @@ int gb_init_shared(gb_ctx** out, const gb_ctx* parent, void* stream)
     ctx->large_chunk_bits = parent->large_chunk_bits;
     ctx->bucket_large = parent->bucket_large;
     ctx->carry_large = parent->carry_large;
+    ctx->carry_cap = parent->carry_cap;
     ctx->fused = parent->fused;
     ctx->mid_limit = parent->mid_limit;
     *out = ctx;

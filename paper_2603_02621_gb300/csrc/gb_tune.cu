@@ -195,16 +195,17 @@ extern "C" int gb_autotune(gb_ctx* ctx, const uint64_t* lo, const uint64_t* hi, 
         Apply apply;
     };
     std::vector<Param> params;
-    // tile and tile / large-prime split together: value = log2(tile) * 8 +
-    // log2(split / tile) + 2 (split from tile / 4 to 16 tiles)
+    // tile and tile / large-prime split together: value = log2(tile) * 16 +
+    // log2(split / tile) + 4 (split from tile / 16 to 16 tiles; at least 2^10)
     {
         std::vector<uint32_t> ts;
         for (uint32_t lt = 16; lt <= 20; ++lt)
-            for (uint32_t m = 0; m <= 6; ++m) ts.push_back(lt * 8 + m);
+            for (uint32_t m = 0; m <= 8; ++m) ts.push_back(lt * 16 + m);
         params.push_back({ts, [](gb_config& c, uint32_t v) {
-                              const uint32_t lt = v / 8, m = v % 8;
+                              const uint32_t lt = v / 16, m = v % 16;
                               c.tile_bits = 1u << lt;
-                              const uint64_t split = (1ull << lt) << m >> 2;
+                              const uint64_t split = (1ull << lt) << m >> 4;
+                              if (split < (1u << 10)) return false;
                               c.bucket_split = (uint32_t)std::min<uint64_t>(split, 0xffffffffull);
                               return true;
                           }});

@@ -129,3 +129,20 @@ def test_carry_strike_counter_equals_the_oracle(gbm, monkeypatch, oracle, A, nbi
     want = (oracle.count_strikes(A, nbits, 47, (1 << 20) - 1) + oracle.count_strikes_coprime15(A, nbits, 1 << 20, r0)
             + oracle.count_strikes(A, nbits, r0 + 1, r1))
     assert w["sieve_strikes"] + w["large_strikes"] == want
+
+
+@pytest.mark.parametrize("cap", [1, 64])
+def test_carry_full_columns_strike_through(gbm, monkeypatch, cap):
+    """Bucket columns far too small (GB_CARRY_CAP): most carried primes find
+    their column full and strike the rest of the window at once; the bits
+    are the same as the per-chunk restart's."""
+    A, nbits = 4 * 10**18 - 10**11 + 1, (1 << 29) + 12345
+    monkeypatch.setenv("GB_CARRY_CAP", str(cap))
+    monkeypatch.delenv("GB_LARGE", raising=False)
+    with gbm.Context(device=0, base_limit=1 << 31, p1=1 << 15, p2=1 << 20) as g:
+        qc, pc = _sieve(g, A, nbits)
+    monkeypatch.delenv("GB_CARRY_CAP")
+    with _ctx(gbm, monkeypatch, "atomic") as g:
+        qa, pa = _sieve(g, A, nbits)
+    np.testing.assert_array_equal(qc, qa)
+    assert pc == pa
