@@ -116,30 +116,73 @@ __device__ __forceinline__ void run_block(std::integer_sequence<int, J...>, cons
     (block_step<K0 + J, K0, NR, KH>(R, C, cum, wt), ...);
 }
 
-// add one block's histogram (cumulative counts, warp-reduced) to shist; kmax
-// becomes the largest bin (prime index + 1) the block added to, if any
+// add one block's histogram to shist; kmax becomes the largest bin (prime
+// index + 1) the block added to, if any.  The lanes' cumulative counts are
+// summed over the warp by a transposed butterfly: two counts per register as
+// 16-bit fields (a lane's counts are at most 960, a warp's at most 30720), and
+// at each of five shuffle stages a lane keeps half of its registers and sends
+// the other half to its partner, so that lane l ends with the warp totals of
+// the counts 2l and 2l + 1 (L / 2 = 32 registers, padded from 24 for L = 48)
+// or, for L = 32, of the counts 2(l/2) and 2(l/2) + 1 (lanes l and l ^ 1
+// alike).  The bins are the differences of consecutive totals.
 template <int K0, int L, int KH>
 __device__ __forceinline__ void flush_block(const uint32_t (&cum)[KH], uint32_t init_pop, uint32_t* shist, int lane,
                                             uint32_t& kmax)
 {
-    uint32_t prev = __reduce_add_sync(0xffffffffu, init_pop);
+    constexpr int NP = L / 2;                               // count pairs
+    constexpr int NR = NP <= 16 ? 16 : 32;                  // registers, a power of two
+    static_assert(L % 2 == 0 && NP <= NR, "block length");
+    uint32_t P[NR];
 #pragma unroll
-    for (int j = 0; j < L; ++j) {
-        const uint32_t v = (cum[j / 3] >> (kCumBits * (j % 3))) & kCumMask;
-        const uint32_t tot = __reduce_add_sync(0xffffffffu, v);
-        if (tot != prev) {
-            if (lane == 0) atomicAdd(&shist[K0 + j + 1], tot - prev);
-            kmax = K0 + j + 1;
+    for (int r = 0; r < NR; ++r) {
+        if (r < NP) {
+            const uint32_t lo = (cum[(2 * r) / 3] >> (kCumBits * ((2 * r) % 3))) & kCumMask;
+            const uint32_t hi = (cum[(2 * r + 1) / 3] >> (kCumBits * ((2 * r + 1) % 3))) & kCumMask;
+            P[r] = lo | (hi << 16);
+        } else {
+            P[r] = 0;
         }
-        prev = tot;
     }
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const unsigned o = 16u >> st;
+        const int m = NR >> (st + 1);                       // registers kept after this stage
+        if (m > 0) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int r = 0; r < (m > 0 ? m : 1); ++r) {
+                const uint32_t send = up ? P[r] : P[r + m];
+                const uint32_t keep = up ? P[r + m] : P[r];
+                P[r] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        } else {
+            P[0] += __shfl_xor_sync(0xffffffffu, P[0], o);
+        }
+    }
+    const uint32_t pi = NR == 32 ? (uint32_t)lane : (uint32_t)lane >> 1;    // this lane's pair
+    const uint32_t t_lo = P[0] & 0xffffu, t_hi = P[0] >> 16;
+    const uint32_t before = __reduce_add_sync(0xffffffffu, init_pop);       // total before the block
+    const uint32_t up_hi = __shfl_up_sync(0xffffffffu, t_hi, NR == 32 ? 1 : 2);
+    const uint32_t prev = pi == 0 ? before : up_hi;
+    uint32_t cand = 0;
+    if (pi < (uint32_t)NP && (NR == 32 || (lane & 1) == 0)) {
+        const uint32_t d_lo = t_lo - prev, d_hi = t_hi - t_lo;
+        if (d_lo) atomicAdd(&shist[K0 + 2 * pi + 1], d_lo);
+        if (d_hi) atomicAdd(&shist[K0 + 2 * pi + 2], d_hi);
+        cand = d_hi ? K0 + 2 * pi + 2 : d_lo ? K0 + 2 * pi + 1 : 0;
+    }
+    const uint32_t top = __reduce_max_sync(0xffffffffu, cand);
+    if (top) kmax = top;
 }
 
 // ---------------------------------------------------------------------------
 // block 0 on three consecutive words per lane: one window serves the three
-// words, so a step is three funnel shifts, three ORs and the three words'
-// popcounts added into the step's counter.  (A carry-save adder would need
-// two popcounts instead of three, at two more logic ops; measured the same.)
+// words, so a step is three funnel shifts and three ORs, then the three
+// words' popcounts added into the step's counter through a carry-save adder:
+// popc(C0) + popc(C1) + popc(C2) = popc(x) + 2 popc(y) with x the sum bits and
+// y the carry bits, two popcounts instead of three for two more logic ops
+// (the popcounts bound the step: measured 8.15 against 9.19 ms for the cover
+// of 2^34 even n near 5e11).
 // Window: R[t] = Q32[w + 2 + d_3/32 - t] for the lane's first word w.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int block0_regs3(int L0) { return (int)((step_e(L0 - 1) + 31) / 32) + 3; }
@@ -168,9 +211,12 @@ __device__ __forceinline__ void step3(const uint32_t (&R)[NR3], uint32_t& C0, ui
     C1 |= s1;
     C2 |= s2;
     const uint32_t w = wt[K % 3];
-    cum[K / 3] = __popc(C0) * w + cum[K / 3];
-    cum[K / 3] = __popc(C1) * w + cum[K / 3];
-    cum[K / 3] = __popc(C2) * w + cum[K / 3];
+    const uint32_t x = C0 ^ C1 ^ C2;                        // sum bits
+    const uint32_t y = (C0 & C1) | (C2 & (C0 | C1));        // carry bits (majority)
+    const uint32_t py = __popc(y);
+    cum[K / 3] = __popc(x) * w + cum[K / 3];
+    cum[K / 3] = py * w + cum[K / 3];                       // twice: weight 2
+    cum[K / 3] = py * w + cum[K / 3];
 }
 
 template <int NR3, int KH, int... J>
