@@ -751,11 +751,12 @@ bool cover_prefix_valid(int KA)
 
 int cover_fast_phase_primes(uint32_t K, uint64_t n_hi)
 {
-    // by magnitude (measured on windows of 2^33 even n near 1e10, 1e12 and
-    // 4e18): 48 + 2 x 32, 64 + 2 x 32, 48 + 4 x 32 primes; the share of 32-n
-    // words still open after 48 primes is about 0.31 near 1e10, after 80
-    // about 0.05, after 112 about 0.003
-    int ka = n_hi < 100000000000ull ? 112 : n_hi < 10000000000000000ull ? 128 : 176;
+    // by magnitude (cover of 2^34 even n timed for KA = 112 .. 240 near 1e10,
+    // 1e11, 5e11, 1e13, 1e15 and 4e18): 48 + 3 x 32 primes below 1e14, 48 +
+    // 4 x 32 below 1e17, 48 + 6 x 32 above; the share of 32-n words still
+    // open after 48 primes is about 0.31 near 1e10, after 80 about 0.05, after
+    // 112 about 0.003
+    int ka = n_hi < 100000000000000ull ? 144 : n_hi < 100000000000000000ull ? 176 : 240;
     while (ka >= 48 && (uint32_t)ka > K) ka -= 32;
     if (ka < 48 && K >= 48) ka = 48;                        // the shortest schedule, block 0 alone
     return ka >= 48 ? ka : 0;
