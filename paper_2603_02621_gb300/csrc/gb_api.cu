@@ -163,6 +163,17 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
             if (nmid > nsmall) {
                 gb::LargeArgs ma = la;
                 ma.n_primes = (uint32_t)(nmid - nsmall);
+                // starts from a residue table of the window (16 bytes per
+                // prime, sized once for every prime below the slice limit)
+                // where the slices and primes allow it
+                const uint64_t slices = (nbits + gb::kMidSliceBits - 1) / gb::kMidSliceBits;
+                if (may_alloc && slices <= gb::kMidResSlices && ctx->base->h_primes[nmid - 1] < (1u << 20)) {
+                    const uint64_t cap = ctx->pi(std::min<uint64_t>(ctx->mid_limit, 1u << 20) - 1);
+                    int rc = ctx->mres.ensure((size_t)std::max<uint64_t>(cap, nmid) * 16);
+                    if (rc) return rc;
+                    ma.res = ctx->mres.as<uint4>();
+                    ctx->kernels += 1;                      // the table's kernel
+                }
                 GB_LAUNCH(gb::launch_mid(ma, nbits, ctx->stream));
             }
             la.primes = ctx->base->primes.as<uint32_t>() + nmid;

@@ -129,6 +129,11 @@ struct LargeArgs {
     uint32_t n_primes;
     uint32_t* out;              // window words
     unsigned long long* strikes;    // optional work count
+    // optional (slices only): per prime {p, (-B) mod p, (2 kMidSliceBits) mod p,
+    // floor(2^33 / p)}, filled by launch_mid before the slices run; needs fewer
+    // than kMidResSlices slices and primes below 2^20 (NULL: a Barrett
+    // reduction per prime and slice)
+    uint4* res;
 };
 cudaError_t launch_large(const LargeArgs& a, cudaStream_t s);
 // the same primes struck per slice of the window in shared memory (one
@@ -138,6 +143,8 @@ cudaError_t launch_large(const LargeArgs& a, cudaStream_t s);
 // an SM has, so that the starts -- most of the kernel's instructions -- are
 // as few as they can be.
 constexpr uint32_t kMidSliceBits = 7u << 18;
+// slices per window for the residue starts (slice index x (2 kMidSliceBits mod p) < 2^33)
+constexpr uint32_t kMidResSlices = 1u << 13;
 cudaError_t launch_mid(const LargeArgs& a, uint64_t nbits, cudaStream_t s);
 // Primes from the slice limit to sqrt(B) over a window of several chunks of
 // 2^chunk_log2 bits (gb_large.cu): each prime started once per window and

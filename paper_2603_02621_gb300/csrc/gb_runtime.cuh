@@ -168,6 +168,7 @@ struct gb_ctx {
     uint32_t carry_cap = 0;           // entries per bucket column (GB_CARRY_CAP, a test switch; 0 = sized by estimate)
     bool fused = false;               // sieve and block cover fused per CTA (GB_FUSED=1)
     uint32_t mid_limit = 1u << 20;    // primes from the split below this: per shared-memory slice (GB_MID_LOG2; 0 = off)
+    DevBuf mres;                      // residue table of the slice starts (LargeArgs::res)
     uint32_t fill_grid = 0;           // persistent fill CTAs
     uint32_t bcap = 0;                // entries per (CTA, bucket tile) list
     uint64_t bucket_overflows = 0;    // chunks redone by the atomic kernel

@@ -247,12 +247,20 @@ cudaError_t launch_large(const LargeArgs& a, cudaStream_t s)
 
 // Primes between the tile split and a few slices (kMidSliceBits): each CTA loads one
 // slice of the window (already sieved by the smaller primes) into shared
-// memory, strikes every such prime in it (one Barrett start per prime and
-// slice), and stores it back -- shared-memory atomics instead of one L2
-// request per strike.
+// memory, strikes every such prime in it (one start per prime and slice), and
+// stores it back -- shared-memory atomics instead of one L2 request per strike.
+//
+// The start is the index of the prime's first odd multiple in the slice.  By
+// default it is a Barrett reduction of the slice's 64-bit first number.  With
+// a residue table (RES) the slice s, whose first number is b_s = B + 2 s S,
+// takes (-b_s) mod p = ((-B) mod p - s (2 S mod p)) mod p: a product below
+// 2^33 (s < 2^13, p < 2^20) reduced by one 32-bit multiply-high with
+// floor(2^33 / p), whose quotient is at most two short (two conditional
+// subtractions), in place of the 64 x 64-bit product of the Barrett step.
+template <bool RES>
 __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* words, uint64_t t0,
-                                          const uint32_t* primes, const uint64_t* recip, uint32_t n_primes,
-                                          uint32_t* slice, unsigned long long& nstrike)
+                                          const uint32_t* primes, const uint64_t* recip, const uint4* res,
+                                          uint32_t n_primes, uint32_t* slice, unsigned long long& nstrike)
 {
     const uint64_t rem = nbits - t0;
     const uint32_t nb = rem < kMidSliceBits ? (uint32_t)rem : kMidSliceBits;
@@ -263,18 +271,25 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
     __syncthreads();
     const int64_t b = B + 2 * (int64_t)t0;
     const int64_t last = B + 2 * (int64_t)(t0 + nb - 1);
+    const uint32_t sidx = (uint32_t)(t0 / kMidSliceBits);    // the slice's index (RES: < 2^13)
     // four primes per thread at a time (k, k + T, k + 2T, k + 3T): their loads
-    // and Barrett starts are independent, so their latencies overlap
+    // and starts are independent, so their latencies overlap
     constexpr int U = 4;
     const uint32_t T = blockDim.x;
     for (uint32_t k0 = threadIdx.x; k0 < n_primes; k0 += U * T) {
         uint32_t p[U], i[U];
         uint64_t m[U];
+        uint4 rs[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t k = k0 + u * T;
-            p[u] = k < n_primes ? primes[k] : 0u;
-            m[u] = k < n_primes ? recip[k] : 0ull;
+            if constexpr (RES) {
+                rs[u] = k < n_primes ? res[k] : make_uint4(0u, 0u, 0u, 0u);
+                p[u] = rs[u].x;
+            } else {
+                p[u] = k < n_primes ? primes[k] : 0u;
+                m[u] = k < n_primes ? recip[k] : 0ull;
+            }
         }
         if ((int64_t)((uint64_t)p[0] * p[0]) > last) break;  // ascending primes
 #pragma unroll
@@ -282,7 +297,18 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
             i[u] = nb;                                        // no strike
             const uint64_t pp = (uint64_t)p[u] * p[u];
             if (p[u] && (int64_t)pp <= last) {
-                uint32_t s = first_odd_multiple(b, p[u], m[u]);
+                uint32_t s;
+                if constexpr (RES) {
+                    const uint64_t t = (uint64_t)sidx * rs[u].z;                    // < 2^33
+                    const uint32_t qt = __umulhi((uint32_t)(t >> 1), rs[u].w);      // floor(t / p) - {0, 1, 2}
+                    uint32_t r = (uint32_t)t - qt * p[u];                          // < 3p
+                    if (r >= p[u]) r -= p[u];
+                    if (r >= p[u]) r -= p[u];
+                    const uint32_t x = rs[u].y >= r ? rs[u].y - r : rs[u].y + (p[u] - r);   // (-b) mod p
+                    s = (x & 1u) ? (x + p[u]) >> 1 : x >> 1;                       // x + p < 2^21
+                } else {
+                    s = first_odd_multiple(b, p[u], m[u]);
+                }
                 if ((int64_t)pp > b) {
                     const uint64_t isq = ((uint64_t)((int64_t)pp - b)) >> 1;
                     if (isq > s) s = (uint32_t)isq;           // isq < nb here
@@ -303,12 +329,23 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
     for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) q[w] = slice[w];
 }
 
+// the residue table of one window for the slice starts (see mid_slice)
+__global__ void __launch_bounds__(256) k_mid_residues(const LargeArgs a)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.n_primes) return;
+    const uint32_t p = a.primes[k];
+    a.res[k] = make_uint4(p, neg_mod(a.B, p, a.recip[k]), (uint32_t)((2ull * kMidSliceBits) % p),
+                          (uint32_t)((1ull << 33) / p));
+}
+
+template <bool RES>
 __global__ void __launch_bounds__(1024) k_mid(const LargeArgs a, uint64_t nbits)
 {
     extern __shared__ uint32_t slice[];
     unsigned long long nstrike = 0;
-    mid_slice(a.B, nbits, a.out, (uint64_t)blockIdx.x * kMidSliceBits, a.primes, a.recip, a.n_primes, slice,
-              nstrike);
+    mid_slice<RES>(a.B, nbits, a.out, (uint64_t)blockIdx.x * kMidSliceBits, a.primes, a.recip, a.res, a.n_primes,
+                   slice, nstrike);
     if (a.strikes) {
         for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);
         if ((threadIdx.x & 31) == 0 && nstrike) atomicAdd(a.strikes, nstrike);
@@ -329,8 +366,8 @@ __global__ void __launch_bounds__(1024) k_mid_items(const MidItemsArgs a)
         __syncthreads();
         if (item >= n_items) break;
         const BatchRange r = a.ranges[a.item_range[item]];
-        mid_slice(r.B, r.nbits, a.Q + 2 * r.q_off, (uint64_t)a.item_slice[item] * kMidSliceBits, a.primes, a.recip,
-                  a.n_primes, slice, nstrike);
+        mid_slice<false>(r.B, r.nbits, a.Q + 2 * r.q_off, (uint64_t)a.item_slice[item] * kMidSliceBits, a.primes,
+                         a.recip, nullptr, a.n_primes, slice, nstrike);
     }
     if (a.strikes) {
         for (int o = 16; o; o >>= 1) nstrike += __shfl_xor_sync(0xffffffffu, nstrike, o);
@@ -360,9 +397,18 @@ cudaError_t launch_mid(const LargeArgs& a, uint64_t nbits, cudaStream_t s)
     const uint64_t slices = (nbits + kMidSliceBits - 1) / kMidSliceBits;
     if (slices > 0x7fffffffull) return cudaErrorInvalidValue;
     const size_t smem = (size_t)kMidSliceBits / 8;
-    cudaError_t e = cudaFuncSetAttribute(k_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (a.res) {
+        // residue starts: fewer than 2^13 slices and primes below 2^20
+        if (slices > kMidResSlices) return cudaErrorInvalidValue;
+        k_mid_residues<<<(a.n_primes + 255) / 256, 256, 0, s>>>(a);
+        cudaError_t e = cudaFuncSetAttribute(k_mid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mid<true><<<(unsigned)slices, 1024, smem, s>>>(a, nbits);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_mid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_mid<<<(unsigned)slices, 1024, smem, s>>>(a, nbits);
+    k_mid<false><<<(unsigned)slices, 1024, smem, s>>>(a, nbits);
     return cudaGetLastError();
 }
 
