@@ -29,6 +29,13 @@ __device__ __forceinline__ void strike_word(const uint32_t* sm, uint32_t* w, uin
     atomicAnd(w, mask);
 }
 
+// warp-struck primes below this start each lane at a strike chosen so that the
+// lanes' words fall in distinct shared-memory banks
+#ifndef GB_ROTATE_BELOW
+#define GB_ROTATE_BELOW 128
+#endif
+constexpr uint32_t kRotateBelow = GB_ROTATE_BELOW;
+
 // one stamp table read at pattern offset a (a < period): 32 bits from bit a
 __device__ __forceinline__ uint32_t stamp_word(const uint32_t* tab, uint32_t a)
 {
@@ -119,20 +126,42 @@ __device__ __forceinline__ void sieve_tile(const SieveArgs& a, uint64_t t0, cons
             pending &= pending - 1;
             const uint32_t q = __shfl_sync(0xffffffffu, p, src);
             const uint32_t j0 = __shfl_sync(0xffffffffu, i0, src);
-            // lane l strikes j0 + l q + 32 q k: the step is q whole words, so
+            // lane l strikes j0 + l q + 32 q t: the step is q whole words, so
             // the bit in the word, hence the mask, is fixed per lane
             const uint32_t i = j0 + (uint32_t)lane * q;           // < 2^20 + 2^15: no wrap
             if (i < nb) {
                 const uint32_t mask = __funnelshift_l(0xfffffffeu, 0xfffffffeu, i);
-                uint32_t* w = sm + (i >> 5);
-                uint32_t* const end = sm + ((nb - (i & 31u) + 31u) >> 5);   // words whose bit i&31 is < nb
-                for (; w + 3 * q < end; w += 4 * q) {
-                    strike_word(sm, w, mask, tw);
-                    strike_word(sm, w + q, mask, tw);
-                    strike_word(sm, w + 2 * q, mask, tw);
-                    strike_word(sm, w + 3 * q, mask, tw);
+                const uint32_t w0 = i >> 5;                       // the lane's first word
+                const uint32_t end = (nb - (i & 31u) + 31u) >> 5; // words whose bit i&31 is < nb
+                // For small q a lane's words are many (t up to 2^18 / 32 q) and
+                // the 32 lanes' first words share banks (they lie q/32 words
+                // apart).  Lane l then starts at its strike t = rot with
+                // w0 + rot q = l (mod 32), rot = (l - w0) q^-1 mod 32, runs to the
+                // tile end, and strikes t = rot - 1 down to 0 after: at every step
+                // the lanes' words are then in 32 distinct banks (each lane's
+                // bank moves by the same q or -q per step).
+                uint32_t rot = 0;
+                if (q < kRotateBelow) {
+                    const uint32_t qinv = q * (2u - q * q);       // q^-1 mod 64 (q odd)
+                    rot = (((uint32_t)lane - w0) * qinv) & 31u;
+                    if (w0 + rot * q >= end) rot = 0;             // a short (last) tile: no rotation
                 }
-                for (; w < end; w += q) strike_word(sm, w, mask, tw);
+                uint32_t x = w0 + rot * q;
+                for (; x + 3 * q < end; x += 4 * q) {
+                    strike_word(sm, sm + x, mask, tw);
+                    strike_word(sm, sm + x + q, mask, tw);
+                    strike_word(sm, sm + x + 2 * q, mask, tw);
+                    strike_word(sm, sm + x + 3 * q, mask, tw);
+                }
+                for (; x < end; x += q) strike_word(sm, sm + x, mask, tw);
+                uint32_t n = rot;                                 // then t = rot - 1, ..., 0
+                for (; n >= 4; n -= 4) {
+                    strike_word(sm, sm + w0 + (n - 1) * q, mask, tw);
+                    strike_word(sm, sm + w0 + (n - 2) * q, mask, tw);
+                    strike_word(sm, sm + w0 + (n - 3) * q, mask, tw);
+                    strike_word(sm, sm + w0 + (n - 4) * q, mask, tw);
+                }
+                for (; n > 0; --n) strike_word(sm, sm + w0 + (n - 1) * q, mask, tw);
             }
         }
     }
