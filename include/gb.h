@@ -340,8 +340,12 @@ int gb_verify_range_noalloc(gb_ctx* ctx, uint64_t lo, uint64_t hi, uint32_t P,
  * batched mode: q bits), 2 retry pass (units: even n of the slabs it ran on),
  * 3 reductions and the max-only pass (units: segments), 4 segment sieve,
  * primes above the tile split (units: q bits).  gb_profile_enable resets the
- * counters. */
+ * counters.  enable: 0 off; 1 (or any other nonzero value) event times and
+ * the kernels' work counters (gb_profile_work); GB_PROFILE_EVENTS event
+ * times alone, so that the timed kernels are exactly the ones that run with
+ * profiling off (the work counters cost the strike loops an add per strike). */
 #define GB_PROF_KINDS 5
+#define GB_PROFILE_EVENTS 2
 int gb_profile_enable(gb_ctx* ctx, int enable);
 int gb_profile_read(gb_ctx* ctx, double* ms, uint64_t* launches, uint64_t* units);
 

@@ -587,7 +587,8 @@ int gb_profile_enable(gb_ctx* ctx, int enable)
     ctx->work_strikes = ctx->work_iters = ctx->work_large = 0;
     ctx->kernels = 0;
     ctx->copied_h2d = ctx->copied_d2h = 0;
-    if (enable && !ctx->work.p) {
+    ctx->count_work = enable != 0 && enable != GB_PROFILE_EVENTS;
+    if (ctx->count_work && !ctx->work.p) {
         if ((rc = ctx->work.ensure(24))) return rc;
         GB_CUDA(cudaMemset(ctx->work.p, 0, 24));
     }

@@ -264,7 +264,11 @@ struct gb_ctx {
         pending.push_back({cur_a, b, cur_kind});
         cur_kind = -1;
     }
-    unsigned long long* work_ptr(int i) { return profiling && work.p ? work.as<unsigned long long>() + i : nullptr; }
+    bool count_work = false;          // the kernels count their work (gb_profile_enable 1, not GB_PROFILE_EVENTS)
+    unsigned long long* work_ptr(int i)
+    {
+        return profiling && count_work && work.p ? work.as<unsigned long long>() + i : nullptr;
+    }
     int prof_collect()
     {
         if (work.p) {

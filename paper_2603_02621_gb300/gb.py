@@ -256,11 +256,15 @@ def _verify(fn, name, ctx, lo, hi, P, *, hist_cap, pmin, segs, seg_hist_stride, 
 
 
 GB_PROF_KINDS = 5
+GB_PROFILE_EVENTS = 2                  # gb_profile_enable: event times without the work counters
 PROF_NAMES = ("sieve", "cover", "retry", "reduce", "large")
 
 
-def gb_profile_enable(ctx: int, enable: bool = True) -> None:
-    _check(load().gb_profile_enable(ctx, int(bool(enable))), "gb_profile_enable")
+def gb_profile_enable(ctx: int, enable=True) -> None:
+    """enable: False / 0 off, True / 1 event times and work counters,
+    GB_PROFILE_EVENTS event times alone."""
+    mode = GB_PROFILE_EVENTS if enable == GB_PROFILE_EVENTS and not isinstance(enable, bool) else int(bool(enable))
+    _check(load().gb_profile_enable(ctx, mode), "gb_profile_enable")
 
 
 def gb_profile_read(ctx: int) -> dict:

@@ -29,3 +29,24 @@ def test_generic_cover_iterations_equal_the_oracle(gbm, oracle, lo, hi, P1, S):
         gbm.gb_profile_enable(g.handle, False)
     assert r["n_checked"] == (hi - lo) // 2
     assert w["cover_iterations"] == oracle.cover_iterations(lo, hi, P1)
+
+
+def test_event_only_profiling_counts_no_work(gbm):
+    """GB_PROFILE_EVENTS times the kernels with the work counters off (the
+    timed kernels are the unprofiled ones); mode 1 counts the same call's work;
+    the outputs do not depend on the mode."""
+    lo, hi = 10**12, 10**12 + 2 * (1 << 22)
+    with gbm.Context(device=0, base_limit=1 << 21, seg_len=1 << 20, p1=1 << 15, p2=1 << 20) as g:
+        gbm.gb_profile_enable(g.handle, gbm.GB_PROFILE_EVENTS)
+        r0 = g.verify_range(lo, hi, hist_cap=3512)
+        w0 = gbm.gb_profile_work(g.handle)
+        t0 = gbm.gb_profile_read(g.handle)
+        gbm.gb_profile_enable(g.handle, True)
+        r1 = g.verify_range(lo, hi, hist_cap=3512)
+        w1 = gbm.gb_profile_work(g.handle)
+        gbm.gb_profile_enable(g.handle, False)
+    assert w0 == dict(sieve_strikes=0, cover_iterations=0, large_strikes=0)
+    assert t0["sieve"]["launches"] >= 1 and t0["sieve"]["ms"] > 0 and t0["cover"]["ms"] > 0
+    assert w1["sieve_strikes"] > 0 and w1["cover_iterations"] > 0 and w1["large_strikes"] > 0
+    assert (r0["max_pmin"], r0["max_pmin_n"], r0["unresolved"]) == (r1["max_pmin"], r1["max_pmin_n"], r1["unresolved"])
+    assert (r0["hist"] == r1["hist"]).all()
