@@ -55,11 +55,13 @@ PLAIN_MODES = {
     "window-4e18": dict(lo=4 * 10**18 - 10**11, hi=4 * 10**18, seg=1 << 27, base=1 << 31,
                         workload="Goldbach verification of every even n in the window [4e18 - 1e11, 4e18)"),
 }
-# DRAM bytes per unit (even n) of the dominant kernels, from ncu captures
-# (profiles/): scaled to a launch by the units it processes
+# DRAM bytes per unit of the dominant kernels (cover: even n; sieve and the
+# slices: q bits), from ncu captures of the kernels as built (profiles/):
+# scaled to a launch by the units it processes.  A workload without a capture
+# of the current kernels reports no traffic.
 NCU_TRAFFIC = {
-    "plain": {"cover": 0.1270, "sieve": 0.09678},                 # [4, 2^32] (profiles/k_*_4_to_2e32.md)
-    "exhaustive-1e12": {"cover": 0.1270, "sieve": 0.09684},       # 2^31 n near 1e12 (profiles/k_*_1e12.md)
+    # 2^31 even n near 1e12 (profiles/k_cover_fast_1e12.md, k_sieve_1e12.md, k_mid_1e12.md)
+    "exhaustive-1e12": {"cover": 0.12672, "sieve": 0.09684, "large": 0.22365},
 }
 
 
