@@ -71,7 +71,8 @@ def test_roofline_arithmetic():
     """The roofline of the bench line, from a synthetic profile: the dominant
     kernel by total time; achieved = algorithmic ALU ops per launch over the
     launch's time; frac = achieved / (SMs x 64 lanes x clock); traffic =
-    the ncu bytes per unit times the units of one launch (plain workload only)."""
+    the ncu bytes per unit times the units of one launch (workloads with a
+    capture of the current kernels only)."""
     sys.path.insert(0, ROOT)
     import bench
     steps, nl = 10, 10
@@ -82,13 +83,14 @@ def test_roofline_arithmetic():
     alg_cover = 3.9e9                                                       # per step
     peaks = {"sm_max_mhz": 2070.0, "hbm_gbs": 6695.5}
     sms = 152
-    r = bench.roofline_of(prof, wk, alg_cover, steps, "plain", peaks, "measured", sms)
+    r = bench.roofline_of(prof, wk, alg_cover, steps, "exhaustive-1e12", peaks, "measured", sms)
     peak = sms * 64 * 2070e6 / 1e12
     assert r["kernel"] == "cover" and r["bound"] == "alu" and abs(r["peak"] - peak) < 1e-9
     ops = 4.0 * alg_cover * steps / nl
     achieved = ops / (23.3 / nl / 1000.0) / 1e12
     assert abs(r["achieved"] - achieved) < 1e-9 * achieved and abs(r["frac"] - achieved / peak) < 1e-12
-    assert abs(r["traffic"] - 0.1270 * 5.0e10 / nl) < 1e-3
+    assert abs(r["traffic"] - bench.NCU_TRAFFIC["exhaustive-1e12"]["cover"] * 5.0e10 / nl) < 1e-3
+    assert bench.roofline_of(prof, wk, alg_cover, steps, "plain", peaks, "measured", sms)["traffic"] is None
     s = r["kernels"]["sieve"]
     assert abs(s["alu_ops_per_launch"] - (2.0 * 5.3e10 / nl + 6.0 * 6.25e10 / nl / 32.0)) < 1.0
     assert abs(s["algorithmic_bytes_per_launch"] - 6.25e10 / nl / 8.0) < 1e-6
