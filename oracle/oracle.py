@@ -81,6 +81,8 @@ def _load():
         lib.or_count_strikes.argtypes = [i64, u64, u64, u64]
         lib.or_count_strikes_coprime15.restype = u64
         lib.or_count_strikes_coprime15.argtypes = [i64, u64, u64, u64]
+        lib.or_count_strikes_coprime105.restype = u64
+        lib.or_count_strikes_coprime105.argtypes = [i64, u64, u64, u64]
         lib.or_prime_pi.restype = u64
         lib.or_prime_pi.argtypes = [u64, ctypes.c_int]
         _lib = lib
@@ -183,6 +185,12 @@ def count_strikes_coprime15(a_odd: int, nbits: int, p_lo: int, p_hi: int) -> int
     """As count_strikes, only the multiples j p with j coprime to 15 (the
     strikes left when the multiples of 3 and 5 are cleared already)."""
     return int(_load().or_count_strikes_coprime15(a_odd, nbits, p_lo, p_hi))
+
+
+def count_strikes_coprime105(a_odd: int, nbits: int, p_lo: int, p_hi: int) -> int:
+    """As count_strikes, only the multiples j p with j coprime to 105 (the
+    strikes left when the multiples of 3, 5 and 7 are cleared already)."""
+    return int(_load().or_count_strikes_coprime105(a_odd, nbits, p_lo, p_hi))
 
 
 def cover_iterations(lo: int, hi: int, P: int) -> int:

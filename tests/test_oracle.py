@@ -273,6 +273,40 @@ def test_strike_count_coprime15_brute_force(oracle, a, nbits, plo, phi):
         assert got < oracle.count_strikes(a, nbits, plo, phi) or want == 0
 
 
+@pytest.mark.parametrize("a,nbits,plo,phi", [
+    (1, 5000, 3, 1000),
+    (10**6 + 1, 3001, 47, 10**6),
+    (10**9 + 7, 999, 5, 31),
+    (-41, 300, 3, 100),
+    (10**12 + 1, 4001, 7, 10**6),
+    (4 * 10**18 - 10**11 + 1, 2001, 1 << 20, 1 << 22),
+])
+def test_strike_count_coprime105_brute_force(oracle, a, nbits, plo, phi):
+    # every odd number m = j p of the window, p in range, m >= p^2, with the
+    # cofactor j coprime to 105
+    last = a + 2 * (nbits - 1)
+    r = min(phi, math.isqrt(max(last, 0)))
+    if a > 10**15:
+        # too far for a prime list to sqrt: test each candidate factor p of m
+        # directly, with p prime by trial division (p < 2^22)
+        cands = [p for p in range(plo | 1, r + 1, 2) if oracle.mr_isprime(p)]
+    else:
+        cands = [p for p in oracle.primes_upto(r).tolist() if p >= plo and p > 2]
+    want = 0
+    for p in cands:
+        j0 = max(-(-max(a, 4) // p), p)
+        j0 += (j0 + 1) % 2                       # odd cofactor (m odd)
+        for j in range(j0, last // p + 1, 2):
+            if math.gcd(j, 105) == 1:
+                want += 1
+    got = oracle.count_strikes_coprime105(a, nbits, plo, phi)
+    assert got == want
+    # the cofactors coprime to 15 but divisible by 7 are the difference
+    extra = sum(1 for p in cands for j in range(max(-(-max(a, 4) // p), p), last // p + 1)
+                if j % 2 and math.gcd(j, 15) == 1 and j % 7 == 0)
+    assert oracle.count_strikes_coprime15(a, nbits, plo, phi) - got == extra
+
+
 def test_cover_iterations_worked_by_hand(oracle):
     # one 64-n word, n = 4 .. 130: the largest p_min there is 19 (at n = 98
     # and n = 128: n - 3, ..., n - 17 are all composite, n - 19 is prime),
