@@ -77,9 +77,9 @@ int tile_sieve_args(gb_ctx* ctx, int64_t B, uint64_t nbits, gb::SieveArgs& a, ui
 // window (B, nbits), struck chunk by chunk of 2^clog2 bits with each prime
 // started once and carried (gb_large.cu): the primes below half a chunk in
 // per-prime words, the larger ones in a ring of per-chunk buckets.  A bucket
-// holds at most the primes with a multiple m p (m coprime to 30) in one
-// chunk: C (8/15) sum 1/p, which Mertens' theorem puts at
-// C (8/15) (ln ln p_hi - ln ln p_lo); an entry that still finds its bucket
+// holds at most the primes with a multiple m p (m coprime to 210) in one
+// chunk: C (48/105) sum 1/p, which Mertens' theorem puts at
+// C (48/105) (ln ln p_hi - ln ln p_lo); an entry that still finds its bucket
 // full is struck through to the window's end by the kernel itself.
 static int carry_large(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, uint64_t k0, uint64_t k1,
                        uint32_t clog2)
@@ -91,7 +91,7 @@ static int carry_large(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, ui
     a.nbits = nbits;
     a.chunk_log2 = clog2;
     a.nchunks = (uint32_t)((nbits + C - 1) >> clog2);
-    a.B_mod30 = (uint32_t)(B % 30);
+    a.B_mod210 = (uint32_t)(B % 210);
     a.primes = ctx->base->primes.as<uint32_t>() + k0;
     a.recip = ctx->base->recip.as<uint64_t>() + k0;
     a.n_dense = (uint32_t)(kd - k0);
@@ -100,23 +100,25 @@ static int carry_large(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, ui
     a.grid = gb::carry_grid();
     if (a.n_sparse) {
         const double p_lo = (double)ctx->base->h_primes[kd], p_hi = (double)ctx->base->h_primes[k1 - 1];
-        // an entry moves at most 1 + 3 p / C chunks ahead; the bucket being
-        // drained and the one drained before it must stay out of reach
-        const uint64_t adv = 1 + ((3ull * ctx->base->h_primes[k1 - 1]) >> clog2);
+        // an entry moves at most 1 + 5 p / C chunks ahead (half gaps of the
+        // wheel up to 5); the bucket being drained and the one drained before
+        // it must stay out of reach
+        const uint64_t adv = 1 + ((5ull * ctx->base->h_primes[k1 - 1]) >> clog2);
         while (R < adv + 2) R <<= 1;
         if (R > gb::kCarryMaxRing) return fail(GB_EINVAL, "internal: carried primes reach too many chunks ahead");
         // each CTA's column holds its share (1 / grid) of a bucket
-        const double M = (double)C * (8.0 / 15.0) * (std::log(std::log(p_hi)) - std::log(std::log(p_lo)) + 1.0 / p_lo) /
-                         a.grid;
+        const double M = (double)C * (48.0 / 105.0) *
+                         (std::log(std::log(p_hi)) - std::log(std::log(p_lo)) + 1.0 / p_lo) / a.grid;
         a.cap = (uint32_t)std::min(2.0e9, 1.15 * M + 8.0 * std::sqrt(M) + 64.0);
         if (ctx->carry_cap) a.cap = ctx->carry_cap;           // (test switch: small columns spill)
     }
     const size_t ncnt = (size_t)R * a.grid;
     int rc;
-    if ((a.n_dense && (rc = ctx->cstate.ensure((size_t)a.n_dense * 4))) ||
+    if ((a.n_dense && ((rc = ctx->cstate.ensure((size_t)a.n_dense * 4)) || (rc = ctx->cpos.ensure(a.n_dense)))) ||
         (a.n_sparse && (rc = ctx->cring.ensure(ncnt * a.cap * 8))) || (rc = ctx->ccnt.ensure((ncnt + 1) * 4)))
         return rc;
     a.dstate = ctx->cstate.as<uint32_t>();
+    a.dpos = ctx->cpos.as<uint8_t>();
     a.ring = ctx->cring.as<uint64_t>();
     a.ring_cnt = ctx->ccnt.as<uint32_t>();
     a.ring_mask = R - 1;
@@ -237,7 +239,9 @@ int run_sieve(gb_ctx* ctx, int64_t B, uint64_t nbits, uint32_t* out, unsigned lo
         uint64_t natomic = nmid;
         const uint32_t clog2 = 28;
         if (nbucket_lo > nmid && ctx->carry_large && may_alloc && B > 0 && (nbits >> clog2) >= 2) {
-            const uint64_t kb1 = std::min<uint64_t>(nbucket_lo, std::max<uint64_t>(nmid, ctx->pi(isqrt_u64((uint64_t)B))));
+            // (carried primes below 2^31: a bucket entry holds p / 2 in 30 bits)
+            const uint64_t kb1 = std::min<uint64_t>(std::min<uint64_t>(nbucket_lo, ctx->pi(0x7fffffffu)),
+                                                    std::max<uint64_t>(nmid, ctx->pi(isqrt_u64((uint64_t)B))));
             if (kb1 > nmid) {
                 int rc = carry_large(ctx, B, nbits, out, nmid, kb1, clog2);
                 if (rc) return rc;

@@ -150,20 +150,21 @@ cudaError_t launch_mid(const LargeArgs& a, uint64_t nbits, cudaStream_t s);
 // 2^chunk_log2 bits (gb_large.cu): each prime started once per window and
 // carried from chunk to chunk -- per-prime next-multiple words for the primes
 // below half a chunk, a ring of per-chunk buckets for the larger ones -- with
-// the multiples m p, m coprime to 30, struck by global atomic AND.
+// the multiples m p, m coprime to 210, struck by global atomic AND.
 struct BucketLargeArgs {
     int64_t  B;                 // odd number of bit 0 of the window, with p^2 <= B for every prime
     uint64_t nbits;             // window bits
     uint32_t chunk_log2;        // chunk bits 2^chunk_log2 (<= 2^28)
     uint32_t nchunks;           // ceil(nbits / chunk)
-    uint32_t B_mod30;           // B mod 30
-    const uint32_t* primes;     // [0, n_dense): below half a chunk; then n_sparse larger ones
+    uint32_t B_mod210;          // B mod 210
+    const uint32_t* primes;     // [0, n_dense): below half a chunk; then n_sparse larger ones, all below 2^31
     const uint64_t* recip;      // their Barrett reciprocals
     uint32_t n_dense, n_sparse;
-    uint32_t* dstate;           // [n_dense]: next multiple's offset in the current chunk | wheel position << 29
-    uint64_t* ring;             // [R][grid][cap] entries: p << 32 | wheel position << 28 | offset in the chunk
+    uint32_t* dstate;           // [n_dense]: next multiple's offset in the current chunk
+    uint8_t* dpos;              // [n_dense]: its wheel position (0 .. 47, mod 210)
+    uint64_t* ring;             // [R][grid][cap] entries: p / 2 << 34 | wheel position << 28 | offset in the chunk
     uint32_t* ring_cnt;         // [R][grid] entries per bucket column (zeroed before the start kernel)
-    uint32_t ring_mask;         // R - 1; R > 1 + 3 max(p) / chunk + 1, R <= kCarryMaxRing
+    uint32_t ring_mask;         // R - 1; R > 1 + 5 max(p) / chunk + 1, R <= kCarryMaxRing
     uint32_t grid;              // CTAs of every launch (carry_grid()): one bucket column each
     uint32_t cap;               // entries per bucket column
     uint32_t* out;              // window words

@@ -164,7 +164,7 @@ struct gb_ctx {
     // primes from mid_limit to sqrt(B) carried from chunk to chunk (gb_large.cu)
     // for windows of at least two chunks (GB_LARGE=atomic: restarted per chunk)
     bool carry_large = true;
-    DevBuf cstate, cring, ccnt;       // dense next-multiple words; bucket ring; bucket counts + spill count
+    DevBuf cstate, cpos, cring, ccnt; // dense next-multiple offsets and wheel positions; bucket ring; bucket counts + spill count
     uint32_t carry_cap = 0;           // entries per bucket column (GB_CARRY_CAP, a test switch; 0 = sized by estimate)
     bool fused = false;               // sieve and block cover fused per CTA (GB_FUSED=1)
     uint32_t mid_limit = 1u << 20;    // primes from the split below this: per shared-memory slice (GB_MID_LOG2; 0 = off)

@@ -92,7 +92,7 @@ def test_strike_counters_equal_the_oracle(gbm, monkeypatch, oracle, A, nbits, mo
 ])
 def test_carry_equals_atomic(gbm, monkeypatch, oracle, A, nbits):
     """The large primes started once per window and carried from chunk to
-    chunk (default; multiples m p with m coprime to 30) give the same bits as
+    chunk (default; multiples m p with m coprime to 210) give the same bits as
     the per-chunk restart with every odd multiple (GB_LARGE=atomic), and
     sampled bits agree with the oracle's Miller-Rabin."""
     monkeypatch.delenv("GB_LARGE", raising=False)
@@ -114,7 +114,7 @@ def test_carry_equals_atomic(gbm, monkeypatch, oracle, A, nbits):
 ])
 def test_carry_strike_counter_equals_the_oracle(gbm, monkeypatch, oracle, A, nbits):
     """The work counted by the carried large primes: strikes of m p with m
-    coprime to 15 for the primes from 2^20 to sqrt(A); below 2^20 (tile and
+    coprime to 105 for the primes from 2^20 to sqrt(A); below 2^20 (tile and
     slices) and above sqrt(A) (p^2 inside the window) every odd multiple."""
     import math
     monkeypatch.delenv("GB_LARGE", raising=False)
@@ -126,7 +126,7 @@ def test_carry_strike_counter_equals_the_oracle(gbm, monkeypatch, oracle, A, nbi
         gbm.gb_profile_enable(g.handle, False)
     last = A + 2 * (nbits - 1)
     r0, r1 = math.isqrt(A), math.isqrt(last)
-    want = (oracle.count_strikes(A, nbits, 47, (1 << 20) - 1) + oracle.count_strikes_coprime15(A, nbits, 1 << 20, r0)
+    want = (oracle.count_strikes(A, nbits, 47, (1 << 20) - 1) + oracle.count_strikes_coprime105(A, nbits, 1 << 20, r0)
             + oracle.count_strikes(A, nbits, r0 + 1, r1))
     assert w["sieve_strikes"] + w["large_strikes"] == want
 
@@ -146,3 +146,27 @@ def test_carry_full_columns_strike_through(gbm, monkeypatch, cap):
         qa, pa = _sieve(g, A, nbits)
     np.testing.assert_array_equal(qc, qa)
     assert pc == pa
+
+
+def test_carry_stops_below_2_31(gbm, monkeypatch, oracle):
+    """Above 2^62 the sieving primes pass 2^31; a bucket entry holds p / 2 in
+    30 bits, so the carried primes stop at 2^31 and the larger ones restart
+    in every chunk.  A range near 8e18 whose q window spans two chunks: every
+    segment's record and histogram row equal the per-chunk restart's
+    (GB_LARGE=atomic), and one seeded segment equals the oracle's."""
+    lo, hi, S = 8 * 10**18, 8 * 10**18 + 2 * (1 << 29), 1 << 24
+    kw = dict(hist_cap=3512, segs=True, seg_hist_stride=3512)
+    monkeypatch.delenv("GB_LARGE", raising=False)
+    with gbm.Context(device=0, base_limit=1 << 32, seg_len=S, p1=1 << 15, p2=1 << 20) as g:
+        rc = g.verify_range(lo, hi, **kw)
+    with _ctx(gbm, monkeypatch, "atomic", base_limit=1 << 32, seg_len=S) as g:
+        ra = g.verify_range(lo, hi, **kw)
+    rec = lambda r: [(s["n_checked"], s["unresolved"], s["max_pmin"], s["max_pmin_n"]) for s in r["segs"]]
+    assert rec(rc) == rec(ra) and len(rc["segs"]) == 32
+    np.testing.assert_array_equal(rc["seg_hist"], ra["seg_hist"])
+    from paper_2603_02621_gb300.workloads import sample_indices
+    k = int(sample_indices(32, 1, seed=5)[0])
+    s = rc["segs"][k]
+    summ, hist = oracle.verify_segments(s["lo"], s["hi"], S, 1 << 20, 3512)
+    assert [s["n_checked"], s["unresolved"], s["max_pmin"], s["max_pmin_n"]] == summ[0].tolist()
+    np.testing.assert_array_equal(rc["seg_hist"][k], hist[0])
