@@ -257,6 +257,23 @@ cudaError_t launch_large(const LargeArgs& a, cudaStream_t s)
 // 2^33 (s < 2^13, p < 2^20) reduced by one 32-bit multiply-high with
 // floor(2^33 / p), whose quotient is at most two short (two conditional
 // subtractions), in place of the 64 x 64-bit product of the Barrett step.
+// nw words from src to dst by the whole CTA: 16-byte vectors, several in
+// flight per thread, when both are 16-byte aligned (the slice is one CTA per
+// SM: its load and store are not hidden behind another CTA's strikes)
+__device__ __forceinline__ void copy_slice(uint32_t* dst, const uint32_t* src, uint32_t nw)
+{
+    uint32_t w0 = 0;
+    if ((((uintptr_t)dst | (uintptr_t)src) & 15u) == 0) {
+        const uint32_t nv = nw / 4;
+        uint4* dv = reinterpret_cast<uint4*>(dst);
+        const uint4* sv = reinterpret_cast<const uint4*>(src);
+#pragma unroll 7
+        for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) dv[v] = sv[v];
+        w0 = 4 * nv;
+    }
+    for (uint32_t w = w0 + threadIdx.x; w < nw; w += blockDim.x) dst[w] = src[w];
+}
+
 template <bool RES>
 __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* words, uint64_t t0,
                                           const uint32_t* primes, const uint64_t* recip, const uint4* res,
@@ -267,7 +284,7 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
     const uint32_t nw = (nb + 31) / 32;
     uint32_t* q = words + t0 / 32;
     __syncthreads();                                          // slice free
-    for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) slice[w] = q[w];
+    copy_slice(slice, q, nw);
     __syncthreads();
     const int64_t b = B + 2 * (int64_t)t0;
     const int64_t last = B + 2 * (int64_t)(t0 + nb - 1);
@@ -326,7 +343,7 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
         }
     }
     __syncthreads();
-    for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) q[w] = slice[w];
+    copy_slice(q, slice, nw);
 }
 
 // the residue table of one window for the slice starts (see mid_slice)
