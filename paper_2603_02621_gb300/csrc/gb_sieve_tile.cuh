@@ -36,6 +36,17 @@ __device__ __forceinline__ void strike_word(const uint32_t* sm, uint32_t* w, uin
 #endif
 constexpr uint32_t kRotateBelow = GB_ROTATE_BELOW;
 
+// Wheel mod 30 for the one-thread primes: the stamp has cleared the multiples
+// of 3 and 5, so only m p with m coprime to 30 is struck (8 of every 15 odd m).
+// Positions 0..7 are the coprime residues 1, 7, 11, 13, 17, 19, 23, 29; nibble
+// w of kHalfGaps30 is half the gap from position w to the next (the bit index
+// (m p - b) / 2 then grows by p times it).  For an odd residue m = 2j + 1 of
+// the first multiple, kNextPos30 (3 bits at 3j) is the position of the first
+// coprime residue >= m and kNextHalf30 (2 bits at 2j) half the distance to it.
+constexpr uint32_t kHalfGaps30 = 0x13212123u;
+constexpr uint64_t kNextPos30 = 0x1ffdac8d2248ull;
+constexpr uint32_t kNextHalf30 = 0x6104118u;
+
 // one stamp table read at pattern offset a (a < period): 32 bits from bit a
 __device__ __forceinline__ uint32_t stamp_word(const uint32_t* tab, uint32_t a)
 {
@@ -166,8 +177,11 @@ __device__ __forceinline__ void sieve_tile(const SieveArgs& a, uint64_t t0, cons
         }
     }
     // 2b. larger primes, one thread each; four at a time per thread (k, k +
-    // NT, k + 2 NT, k + 3 NT), so that their loads and Barrett starts overlap
+    // NT, k + 2 NT, k + 3 NT), so that their loads and Barrett starts overlap.
+    // Below 2^20 they step through the mod-30 wheel: fewer strikes, hence
+    // fewer of the shared-memory wavefronts the kernel is bound by.
     constexpr int U = 4;
+    const uint32_t bmod30 = pmod_u32(b, 30);
     for (uint32_t k0 = a.n_warp + threadIdx.x; k0 < a.n_primes; k0 += U * NT) {
         uint32_t p[U], s[U];
         uint64_t m[U];
@@ -189,20 +203,39 @@ __device__ __forceinline__ void sieve_tile(const SieveArgs& a, uint64_t t0, cons
                     if (isq > i) i = isq;
                 }
                 s[u] = i;
-                if (a.strikes && i < nb) nstrike += (nb - 1 - i) / p[u] + 1;
+                if (a.strikes && i < nb && p[u] >= (1u << 20)) nstrike += (nb - 1 - i) / p[u] + 1;
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             uint32_t i = s[u];
-            // i < 2^20 and p < 3.1e9 (p^2 < 2^63): i + p cannot wrap
             if (p[u] < (1u << 20)) {
-                for (; i + p[u] < nb; i += 2 * p[u]) {
-                    strike(sm, i, a.tile_bits);
-                    strike(sm, i + p[u], a.tile_bits);
+                if (i < nb) {
+                    // m = (b + 2i) / p: m p = b + 2i (mod 30), m = (b + 2i) p^-1 with
+                    // p^-1 = p^3 (mod 30) (the units mod 30 have exponent 4)
+                    const uint32_t pm = p[u] % 30u;
+                    const uint32_t inv = pm * pm % 30u * pm % 30u;
+                    const uint32_t j = (bmod30 + 2u * (i % 15u)) % 30u * inv % 30u >> 1;
+                    const uint32_t pos = (uint32_t)(kNextPos30 >> (3 * j)) & 7u;
+                    i += p[u] * ((kNextHalf30 >> (2 * j)) & 3u);     // i + 3p < 2^22: no wrap
+                    uint32_t g = __funnelshift_r(kHalfGaps30, kHalfGaps30, 4 * pos);
+                    if (a.strikes) {
+                        for (; i < nb; g = __funnelshift_r(g, g, 4)) {
+                            strike(sm, i, a.tile_bits);
+                            i += p[u] * (g & 15u);
+                            ++nstrike;
+                        }
+                    } else {
+                        for (; i < nb; g = __funnelshift_r(g, g, 4)) {
+                            strike(sm, i, a.tile_bits);
+                            i += p[u] * (g & 15u);
+                        }
+                    }
                 }
+            } else {
+                // i < 2^20 and p < 3.1e9 (p^2 < 2^63): i + p cannot wrap
+                for (; i < nb; i += p[u]) strike(sm, i, a.tile_bits);
             }
-            for (; i < nb; i += p[u]) strike(sm, i, a.tile_bits);
         }
     }
     if (a.strikes) {

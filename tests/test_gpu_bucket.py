@@ -24,6 +24,23 @@ def _ctx(gbm, monkeypatch, mode, **kw):
     return gbm.Context(**cfg)
 
 
+def _tile_strikes(oracle, A, nbits, p_end):
+    """The oracle's count of the strikes the tile sieve and the slices make
+    for the primes 47 .. p_end - 1, with the default tile (2^18 bits): every
+    odd multiple (>= p^2) for the warp-struck primes (below 1024) and for the
+    slices' primes (from the split on), only those with the cofactor coprime
+    to 15 for the one-thread primes between (their mod-30 wheel).  The split
+    is 2^14 once the window's sieving primes reach 2^18, else the tile."""
+    import math
+    last = A + 2 * (nbits - 1)
+    split = 1 << 14 if math.isqrt(last) >= 1 << 18 else 1 << 18
+    top = min(split, p_end)
+    n = oracle.count_strikes(A, nbits, 47, 1023) + oracle.count_strikes_coprime15(A, nbits, 1024, top - 1)
+    if p_end > split:
+        n += oracle.count_strikes(A, nbits, split, p_end - 1)
+    return n
+
+
 def _sieve(g, A, nbits):
     words = (nbits + 63) // 64
     q = torch.full((words,), -1, dtype=torch.int64, device="cuda")
@@ -72,7 +89,8 @@ def test_bucket_window_vs_oracle_full(gbm, monkeypatch, oracle):
 ])
 def test_strike_counters_equal_the_oracle(gbm, monkeypatch, oracle, A, nbits, mode):
     """The work the roofline divides by: the kernels' strike counters equal the
-    oracle's count of (prime, multiple >= p^2) pairs, primes 47..sqrt."""
+    oracle's count of (prime, multiple >= p^2) pairs, primes 47..sqrt (the
+    one-thread primes of the tile: cofactors coprime to 15)."""
     import math
     with _ctx(gbm, monkeypatch, mode) as g:
         q = torch.zeros(((nbits + 63) // 64,), dtype=torch.int64, device="cuda")
@@ -81,7 +99,7 @@ def test_strike_counters_equal_the_oracle(gbm, monkeypatch, oracle, A, nbits, mo
         w = gbm.gb_profile_work(g.handle)
         gbm.gb_profile_enable(g.handle, False)
     last = A + 2 * (nbits - 1)
-    assert w["sieve_strikes"] + w["large_strikes"] == oracle.count_strikes(A, nbits, 47, math.isqrt(last))
+    assert w["sieve_strikes"] + w["large_strikes"] == _tile_strikes(oracle, A, nbits, math.isqrt(last) + 1)
 
 
 @pytest.mark.parametrize("A,nbits", [
@@ -114,8 +132,9 @@ def test_carry_equals_atomic(gbm, monkeypatch, oracle, A, nbits):
 ])
 def test_carry_strike_counter_equals_the_oracle(gbm, monkeypatch, oracle, A, nbits):
     """The work counted by the carried large primes: strikes of m p with m
-    coprime to 105 for the primes from 2^20 to sqrt(A); below 2^20 (tile and
-    slices) and above sqrt(A) (p^2 inside the window) every odd multiple."""
+    coprime to 105 for the primes from 2^20 to sqrt(A); below 2^20 the tile's
+    and the slices' strikes (_tile_strikes), above sqrt(A) (p^2 inside the
+    window) every odd multiple."""
     import math
     monkeypatch.delenv("GB_LARGE", raising=False)
     with gbm.Context(device=0, base_limit=1 << 31, p1=1 << 15, p2=1 << 20) as g:
@@ -126,7 +145,7 @@ def test_carry_strike_counter_equals_the_oracle(gbm, monkeypatch, oracle, A, nbi
         gbm.gb_profile_enable(g.handle, False)
     last = A + 2 * (nbits - 1)
     r0, r1 = math.isqrt(A), math.isqrt(last)
-    want = (oracle.count_strikes(A, nbits, 47, (1 << 20) - 1) + oracle.count_strikes_coprime105(A, nbits, 1 << 20, r0)
+    want = (_tile_strikes(oracle, A, nbits, 1 << 20) + oracle.count_strikes_coprime105(A, nbits, 1 << 20, r0)
             + oracle.count_strikes(A, nbits, r0 + 1, r1))
     assert w["sieve_strikes"] + w["large_strikes"] == want
 
