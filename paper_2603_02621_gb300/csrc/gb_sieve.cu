@@ -257,6 +257,13 @@ cudaError_t launch_large(const LargeArgs& a, cudaStream_t s)
 // 2^33 (s < 2^13, p < 2^20) reduced by one 32-bit multiply-high with
 // floor(2^33 / p), whose quotient is at most two short (two conditional
 // subtractions), in place of the 64 x 64-bit product of the Barrett step.
+// slice primes below this take the mod-30 wheel (their strikes per slice,
+// 1.75 * 2^20 / p, outnumber the wheel's start cost)
+#ifndef GB_MID_WHEEL_BELOW
+#define GB_MID_WHEEL_BELOW (1u << 16)
+#endif
+constexpr uint32_t kMidWheelBelow = GB_MID_WHEEL_BELOW;
+
 // nw words from src to dst by the whole CTA: 16-byte vectors, several in
 // flight per thread, when both are 16-byte aligned (the slice is one CTA per
 // SM: its load and store are not hidden behind another CTA's strikes)
@@ -289,6 +296,7 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
     const int64_t b = B + 2 * (int64_t)t0;
     const int64_t last = B + 2 * (int64_t)(t0 + nb - 1);
     const uint32_t sidx = (uint32_t)(t0 / kMidSliceBits);    // the slice's index (RES: < 2^13)
+    const uint32_t bmod30 = pmod_u32(b, 30);
     // four primes per thread at a time (k, k + T, k + 2T, k + 3T): their loads
     // and starts are independent, so their latencies overlap
     constexpr int U = 4;
@@ -335,10 +343,30 @@ __device__ __forceinline__ void mid_slice(int64_t B, uint64_t nbits, uint32_t* w
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            for (uint32_t j = i[u]; j < nb; j += p[u]) {      // p < 2^31, j < 2^21: no wrap
-                if (GB_DCHECK(j < kMidSliceBits, kDbgMidStrike))
-                    atomicAnd(slice + (j >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, j));
-                ++nstrike;
+            uint32_t j = i[u];
+            if (p[u] < kMidWheelBelow) {
+                // the mod-30 wheel of the tile sieve (only m p with m coprime to
+                // 15), for primes with enough strikes per slice to pay for its start
+                if (j < nb) {
+                    const uint32_t pm = p[u] % 30u;
+                    const uint32_t inv = pm * pm % 30u * pm % 30u;                  // p^-1 mod 30
+                    const uint32_t jr = (bmod30 + 2u * (j % 15u)) % 30u * inv % 30u >> 1;
+                    const uint32_t pos = (uint32_t)(kNextPos30 >> (3 * jr)) & 7u;
+                    j += p[u] * ((kNextHalf30 >> (2 * jr)) & 3u);                 // j + 3p < 2^22
+                    uint32_t g = __funnelshift_r(kHalfGaps30, kHalfGaps30, 4 * pos);
+                    for (; j < nb; g = __funnelshift_r(g, g, 4)) {
+                        if (GB_DCHECK(j < kMidSliceBits, kDbgMidStrike))
+                            atomicAnd(slice + (j >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, j));
+                        j += p[u] * (g & 15u);
+                        ++nstrike;
+                    }
+                }
+            } else {
+                for (; j < nb; j += p[u]) {                   // p < 2^31, j < 2^21: no wrap
+                    if (GB_DCHECK(j < kMidSliceBits, kDbgMidStrike))
+                        atomicAnd(slice + (j >> 5), __funnelshift_l(0xfffffffeu, 0xfffffffeu, j));
+                    ++nstrike;
+                }
             }
         }
     }
