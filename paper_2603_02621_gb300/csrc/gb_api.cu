@@ -432,7 +432,9 @@ int gb_init(gb_ctx** out, const gb_config* cfg)
     ctx->L = std::max<uint64_t>({c.base_limit, c.p1, c.p2});
     // one warp per sieving prime below 2^10 (at least 32 strikes per lane in a
     // 2^18-bit tile); one thread per larger prime (bank-spread strikes)
-    ctx->warp_split = (int)std::min<uint32_t>(1024, c.tile_bits / 64);
+    // one warp per prime below 512 (larger primes: one thread each, through
+    // the mod-30 wheel; measured faster from 512 on than warps without it)
+    ctx->warp_split = (int)std::min<uint32_t>(512, c.tile_bits / 64);
     if (const char* e = getenv("GB_WARP_SPLIT")) ctx->warp_split = atoi(e);
     if (const char* e = getenv("GB_COVER")) ctx->generic_cover = std::string(e) == "generic";
     if (const char* e = getenv("GB_BATCH_GRAPH")) ctx->batch_graph = atoi(e) != 0;
@@ -528,7 +530,7 @@ int gb_set_config(gb_ctx* ctx, const gb_config* cfg)
     if (ctx->stream) GB_CUDA(cudaStreamSynchronize(ctx->stream));
     else GB_CUDA(cudaDeviceSynchronize());
     ctx->cfg = c;
-    if (!getenv("GB_WARP_SPLIT")) ctx->warp_split = (int)std::min<uint32_t>(1024, c.tile_bits / 64);
+    if (!getenv("GB_WARP_SPLIT")) ctx->warp_split = (int)std::min<uint32_t>(512, c.tile_bits / 64);
     return GB_OK;
 }
 

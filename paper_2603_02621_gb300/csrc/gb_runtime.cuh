@@ -307,14 +307,14 @@ struct gb_ctx {
     }
     // tile / large-prime split for a window whose sieving primes reach r: the
     // configured one, else by magnitude -- when primes reach 2^18 the ones
-    // above 2^14 go faster to the 224 KB shared-memory slices (seven times
-    // fewer starts than per 2^18-bit tile) than through the tile sieve
-    // (measured on 2^34 even n near 5e11: 2^16 19.64 ms, 2^15 19.50, 2^14
-    // 19.40, 2^13 19.42)
+    // above 2^13 go faster to the 224 KB shared-memory slices (residue starts,
+    // a wheel below 2^16) than through the tile sieve (measured on 2^34 even
+    // n near 5e11 with the wheels in place: 2^13 15.33 ms per step, 2^14
+    // 15.43, 2^15 15.78)
     uint32_t split(uint64_t r) const
     {
         if (cfg.bucket_split) return cfg.bucket_split;
-        return r >= (1u << 18) ? std::min<uint32_t>(1u << 14, cfg.tile_bits) : cfg.tile_bits;
+        return r >= (1u << 18) ? std::min<uint32_t>(1u << 13, cfg.tile_bits) : cfg.tile_bits;
     }
 };
 

@@ -27,16 +27,16 @@ def _ctx(gbm, monkeypatch, mode, **kw):
 def _tile_strikes(oracle, A, nbits, p_end):
     """The oracle's count of the strikes the tile sieve and the slices make
     for the primes 47 .. p_end - 1, with the default tile (2^18 bits): every
-    odd multiple (>= p^2) for the warp-struck primes (below 1024) and for the
+    odd multiple (>= p^2) for the warp-struck primes (below 512) and for the
     slices' primes from 2^16 on, only those with the cofactor coprime to 15
     for the primes between (the mod-30 wheel of the tile's one-thread primes
     and of the slices' primes below 2^16).  The split between tile and slices
-    is 2^14 once the window's sieving primes reach 2^18, else the tile."""
+    is 2^13 once the window's sieving primes reach 2^18, else the tile."""
     import math
     last = A + 2 * (nbits - 1)
-    split = 1 << 14 if math.isqrt(last) >= 1 << 18 else 1 << 18
+    split = 1 << 13 if math.isqrt(last) >= 1 << 18 else 1 << 18
     wheel_end = min(max(split, 1 << 16), p_end)
-    n = oracle.count_strikes(A, nbits, 47, 1023) + oracle.count_strikes_coprime15(A, nbits, 1024, wheel_end - 1)
+    n = oracle.count_strikes(A, nbits, 47, 511) + oracle.count_strikes_coprime15(A, nbits, 512, wheel_end - 1)
     if p_end > wheel_end:
         n += oracle.count_strikes(A, nbits, wheel_end, p_end - 1)
     return n
